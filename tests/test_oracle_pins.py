@@ -1,0 +1,246 @@
+"""The oracle pinned against things other than itself (CPU only).
+
+* exact finite clusters (state vector vs nested vs double-layer networks),
+* the variational bound from a Lanczos ground state,
+* closed forms: D=1 product states, the Shastry-Sutherland dimer state,
+* decoupled chains, whose energy follows from the MPS transfer matrix,
+* single- vs double-layer CTMRG agreement (Appendix),
+* the projector adjoint vs torch autograd of plain QR+SVD, and the full
+  gradient vs central finite differences,
+* invariants: scale, Euler relation, lattice rotation.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import exact
+from oracle.api import evaluate
+from oracle.ctmrg import ctmrg, init_env, projectors, projectors_plain, from_ring_arrays, to_ring_arrays
+from oracle.energy import energy
+from oracle.nested import DT, nested_cell
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")))
+
+
+def _env0(Lx, Ly, D, chi, d=2, seed=12345):
+    w = W.Workload("t", Lx, Ly, d, D, chi, 0, [], [])
+    return W.initial_environment(w, seed)
+
+
+# ----------------------------------------------------------------------------- exact clusters
+def test_finite_cluster_nested_and_double_equal_state_vector():
+    rng = np.random.default_rng(3)
+    D, d, Lx, Ly = 2, 2, 3, 2
+    sites = [[torch.tensor(rng.standard_normal((d, D, D, D, D))) for _ in range(Lx)] for _ in range(Ly)]
+    psi = exact.state_vector(sites)
+    h = W.heisenberg_bond()
+    for s1, s2 in exact.cluster_bonds(Lx, Ly):
+        i, j = s1[1] * Lx + s1[0], s2[1] * Lx + s2[0]
+        esv = exact.bond_expectation_sv(psi, h, i, j)
+        for rdm in (exact.nested_bond_rdm, exact.double_bond_rdm):
+            r = rdm(sites, s1, s2, d)
+            e = float(torch.einsum("ab,ba", r, torch.tensor(h)) / torch.trace(r))
+            assert abs(e - esv) < 1e-12
+
+
+def test_state_vector_amplitude_by_brute_force():
+    # 2x2 open cluster: amplitude = sum over all virtual indices of the product (Eq. PEPS)
+    rng = np.random.default_rng(4)
+    D, d = 2, 2
+    T = [torch.tensor(rng.standard_normal((d, D, D, D, D))) for _ in range(4)]
+    psi = exact.state_vector([[T[0], T[1]], [T[2], T[3]]])
+    for s in np.ndindex(2, 2, 2, 2):
+        amp = 0.0
+        for a, b, c, e in np.ndindex(D, D, D, D):  # a: (0,0)-(1,0), b: (0,1)-(1,1), c: (0,0)-(0,1), e: (1,0)-(1,1)
+            amp += float(T[0][s[0], 0, 0, a, c] * T[1][s[1], a, 0, 0, e] * T[2][s[2], 0, c, b, 0] * T[3][s[3], b, e, 0, 0])
+        assert abs(amp - float(psi[s])) < 1e-12
+
+
+def test_lanczos_matches_dense_and_bounds_peps_energy():
+    h = W.heisenberg_bond()
+    # dense diagonalisation of a 2x3 open cluster
+    Lx, Ly = 3, 2
+    n = Lx * Ly
+    H = np.zeros((2**n, 2**n))
+    for (x1, y1), (x2, y2) in exact.cluster_bonds(Lx, Ly):
+        i, j = y1 * Lx + x1, y2 * Lx + x2
+        for b in range(2**n):
+            bits = [(b >> (n - 1 - k)) & 1 for k in range(n)]
+            row = bits[i] * 2 + bits[j]
+            for col in range(4):
+                v = h[col, row]
+                if v != 0.0:
+                    nb = list(bits)
+                    nb[i], nb[j] = col // 2, col % 2
+                    H[int("".join(map(str, nb)), 2), b] += v
+    e_dense = np.linalg.eigvalsh(H)[0]
+    assert abs(exact.lanczos_ground(Lx, Ly, h) - e_dense) < 1e-9
+    # variational bound on the 4x4 cluster for a random D=2 PEPS (rotated frame, same spectrum)
+    rng = np.random.default_rng(5)
+    A = torch.tensor(np.abs(rng.standard_normal((2, 2, 2, 2, 2))))
+    sites = [[A] * 4 for _ in range(4)]
+    psi = exact.state_vector(sites)
+    hr = W.heisenberg_bond_rotated()
+    esv = sum(exact.bond_expectation_sv(psi, hr, y1 * 4 + x1, y2 * 4 + x2)
+              for (x1, y1), (x2, y2) in exact.cluster_bonds(4, 4))
+    e0 = exact.lanczos_ground(4, 4, hr)
+    assert esv >= e0 - 1e-9
+    assert abs(exact.lanczos_ground(4, 4, h) - e0) < 1e-8   # rotation is unitary on a bipartite cluster
+
+
+# ----------------------------------------------------------------------------- closed forms
+def test_neel_rotated_product_state():
+    A = W.neel_rotated_site()
+    E, g = evaluate([A], 1, 1, 2, 3, W.heisenberg_terms_rotated(), env0=_env0(1, 1, 1, 2))
+    assert abs(E - GOLDEN["neel_rotated_D1_energy_per_site"]["value"]) < 1e-12
+
+
+def test_d1_product_state_energy_and_gradient_closed_form():
+    rng = np.random.default_rng(11)
+    hs = rng.standard_normal((4, 4))
+    hs = hs + hs.T
+    v = np.array([0.8, -0.45])
+    terms = [W.Term(0, 0, W.BOND_H, 0.7, hs), W.Term(0, 0, W.BOND_V, 1.3, hs)]
+    E, g = evaluate([W.product_site(v)], 1, 1, 2, 4, terms, env0=_env0(1, 1, 1, 2))
+    vt = torch.tensor(v, requires_grad=True)
+    vv = torch.kron(vt, vt)
+    Ec = (0.7 + 1.3) * (vv @ torch.tensor(hs) @ vv) / (vt @ vt) ** 2
+    Ec.backward()
+    assert abs(E - float(Ec.detach())) < 1e-12
+    assert np.abs(g[0].reshape(-1) - vt.grad.numpy()).max() < 1e-10
+
+
+def test_dimer_singlet_state_exact():
+    sites = W.dimer_singlet_sites()
+    pb = []
+    E, _ = evaluate(sites, 2, 2, 8, 6, W.shastry_sutherland_terms(), env0=_env0(2, 2, 2, 8),
+                    grad=False, per_bond=pb)
+    assert abs(E - GOLDEN["ss_dimer_singlet_energy_per_site"]["value"]) < 1e-12
+    assert all(abs(e) < 1e-12 for e in pb[:8])
+    assert all(abs(e - GOLDEN["ss_dimer_singlet_bond"]["value"]) < 1e-12 for e in pb[8:])
+
+
+def test_dimer_peps_is_the_singlet_product_by_state_vector():
+    # the D=2 construction on a 4x2 open strip: every J' pair (A-F, B-C') inside it is a singlet
+    A, B, C, F = [torch.tensor(t) for t in W.dimer_singlet_sites()]
+    sites = [[A, B, A, B], [C, F, C, F]]
+    psi = exact.state_vector(sites)
+    h = W.heisenberg_bond()
+    # A(0,0)-F(1,1) and A(2,0)-F(3,1) are complete singlets inside the strip
+    for (x1, y1, x2, y2) in ((0, 0, 1, 1), (2, 0, 3, 1)):
+        assert abs(exact.bond_expectation_sv(psi, h, y1 * 4 + x1, y2 * 4 + x2) + 0.75) < 1e-12
+
+
+def test_decoupled_chains_match_transfer_matrix():
+    rng = np.random.default_rng(5)
+    D = 2
+    A = np.zeros((2, D, D, D, D))
+    A[:, :, 0, :, 0] = np.abs(rng.standard_normal((2, D, D)))
+    M = A[:, :, 0, :, 0]
+    T = np.einsum("slr,sLR->lLrR", M, M).reshape(D * D, D * D)
+    w, vr = np.linalg.eig(T)
+    R = np.real(vr[:, np.argmax(abs(w))]).reshape(D, D)
+    w2, vl = np.linalg.eig(T.T)
+    L = np.real(vl[:, np.argmax(abs(w2))]).reshape(D, D)
+    h = W.heisenberg_bond_rotated()
+    rho2 = np.einsum("lL,alm,bmr,cLn,dnR,rR->abcd", L, M, M, M, M, R).reshape(4, 4)
+    eH = np.trace(rho2 @ h) / np.trace(rho2)
+    rho1 = np.einsum("lL,alr,cLR,rR->ac", L, M, M, R)
+    rho1 /= np.trace(rho1)
+    eV = np.trace(np.kron(rho1, rho1) @ h)
+    E, _ = evaluate([A], 1, 1, 8, 30, W.heisenberg_terms_rotated(), env0=_env0(1, 1, D, 8), grad=False)
+    assert abs(E - (eH + eV)) < 1e-9
+
+
+def test_trivial_boundary_is_a_fixed_point_of_the_nested_iteration():
+    rng = np.random.default_rng(5)
+    A = torch.tensor(np.abs(rng.standard_normal((2, 2, 2, 2, 2))))
+    sp = []
+    ctmrg(nested_cell([A], 1, 1), 8, 2, env=None, spectra_log=sp)
+    for it in sp:
+        for s in it:
+            assert float(s[1:].abs().max()) < 1e-15
+
+
+# ----------------------------------------------------------------------------- single vs double
+@pytest.mark.parametrize("Lx,Ly", [(1, 1), (2, 2)])
+@pytest.mark.parametrize("cutoff,tol", [(1e-6, 1e-5), (1e-10, 1e-7)])
+def test_single_and_double_layer_agree(Lx, Ly, cutoff, tol, monkeypatch):
+    # Appendix: nested and reduced contraction agree once chi is large enough;
+    # what is left is the truncation of the spectra at the cutoff.
+    import oracle.ctmrg as oc
+    monkeypatch.setattr(oc, "CUTOFF", cutoff)
+    rng = np.random.default_rng(7)
+    D, chi = 2, 16
+    As = [rng.random((2, D, D, D, D)) + 0.1 for _ in range(Lx * Ly)]
+    h = W.heisenberg_bond()
+    terms = [W.Term(x, y, k, 1.0, h) for y in range(Ly) for x in range(Lx) for k in (W.BOND_H, W.BOND_V)]
+    En, _ = evaluate(As, Lx, Ly, chi, 20, terms, env0=_env0(Lx, Ly, D, chi), grad=False)
+    Ed, _ = evaluate(As, Lx, Ly, chi, 20, terms, env0=None, grad=False, layer="double")
+    assert abs(En - Ed) < tol
+
+
+# ----------------------------------------------------------------------------- adjoint and gradient
+@pytest.mark.parametrize("shape", [(12, 8, 4), (8, 12, 4), (10, 10, 5)])
+def test_projector_adjoint_matches_autograd_of_plain_qr_svd(shape):
+    torch.manual_seed(0)
+    nr, nl, chi = shape
+    N = torch.randn(nr, nl, dtype=DT, requires_grad=True)
+    S = torch.randn(nr, nl, dtype=DT, requires_grad=True)
+    wP, wQ = torch.randn(nl, chi, dtype=DT), torch.randn(nl, chi, dtype=DT)
+    P, Q = projectors(N, S, chi)
+    g1 = torch.autograd.grad((P * wP).sum() + (Q * wQ).sum(), (N, S))
+    P2, Q2 = projectors_plain(N, S, chi)
+    sg = torch.sign((P * P2).sum(0)).detach()
+    assert float((P - P2 * sg).abs().max()) < 1e-12
+    g2 = torch.autograd.grad((P2 * sg * wP).sum() + (Q2 * sg * wQ).sum(), (N, S))
+    for a, b in zip(g1, g2):
+        assert float((a - b).norm() / b.norm()) < 1e-9
+
+
+def test_projector_product_reproduces_truncated_density_matrix():
+    torch.manual_seed(1)
+    N = torch.randn(12, 8, dtype=DT)
+    S = torch.randn(12, 8, dtype=DT)
+    P, Q = projectors(N, S, 3)
+    U, s, Vh = torch.linalg.svd(N @ S.T)
+    assert float((N @ P @ Q.T @ S.T - U[:, :3] @ torch.diag(s[:3]) @ Vh[:3]).abs().max()) < 1e-12
+
+
+def test_gradient_matches_central_finite_differences():
+    w = W.config("heis_d2_chi8")
+    env0 = W.initial_environment(w)
+    n_it = 8
+    E, g = evaluate(w.tensors, 1, 1, w.chi, n_it, w.terms, env0=env0)
+    A = w.tensors[0]
+    rng = np.random.default_rng(1001)
+    for _ in range(3):
+        v = rng.standard_normal(A.shape)
+        v /= np.linalg.norm(v)
+        h = 1e-6 * np.linalg.norm(A)
+        Ep, _ = evaluate([A + h * v], 1, 1, w.chi, n_it, w.terms, env0=env0, grad=False)
+        Em, _ = evaluate([A - h * v], 1, 1, w.chi, n_it, w.terms, env0=env0, grad=False)
+        fd = (Ep - Em) / (2 * h)
+        assert abs(fd - (g[0] * v).sum()) < 1e-7 * max(1e-3, abs(fd)) + 1e-9
+
+
+def test_scale_invariance_and_euler_relation():
+    w = W.config("heis_d2_chi8")
+    env0 = W.initial_environment(w)
+    E1, g = evaluate(w.tensors, 1, 1, w.chi, 6, w.terms, env0=env0)
+    E2, _ = evaluate([3.7 * w.tensors[0]], 1, 1, w.chi, 6, w.terms, env0=env0, grad=False)
+    assert abs(E1 - E2) < 1e-12
+    assert abs((g[0] * w.tensors[0]).sum()) < 1e-10 * np.abs(g[0]).sum()
+
+
+def test_ring_array_roundtrip():
+    w = W.config("ss_d6_chi64")
+    w = W.Workload("s", 2, 2, 2, 2, 4, 0, [], [])
+    arr = W.initial_environment(w)
+    env = from_ring_arrays(arr, 4, 4)
+    back = to_ring_arrays(env)
+    assert all(np.array_equal(a, b) for s1, s2 in zip(arr, back) for a, b in zip(s1, s2))

@@ -1,0 +1,248 @@
+"""Seeded synthetic inputs shared by the oracle and the CUDA path.
+
+This module holds no arithmetic of the method: it only draws site tensors,
+writes down the spin-1/2 bond operators of the two lattice models, and lists
+the bond terms of each workload.  Both the oracle (``oracle/``) and the CUDA
+path read their inputs from here, so that the two sides see identical data.
+
+Conventions
+-----------
+* A site tensor is a float64 array ``A[s, l, u, r, d]`` (physical index first,
+  then the four virtual legs left, up, right, down), row-major.
+* PEPS site ``(x, y)`` of an ``Lx x Ly`` unit cell (x to the right, y down) is
+  stored at index ``y * Lx + x``.
+* A bond operator ``h`` is a real ``d^2 x d^2`` matrix, row index
+  ``s1 * d + s2`` and column index ``s1' * d + s2'``, where site 1 is the
+  first site of the bond (left, top, or as listed for the diagonal kinds).
+* Bond kinds (both endpoints given relative to ``(x, y)``):
+  ``H``: (x, y)-(x+1, y); ``V``: (x, y)-(x, y+1);
+  ``DIAG_DR``: (x, y)-(x+1, y+1); ``DIAG_UR``: (x+1, y)-(x, y+1).
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+
+BOND_H, BOND_V, BOND_DIAG_DR, BOND_DIAG_UR = 0, 1, 2, 3
+BOND_NAMES = {BOND_H: "H", BOND_V: "V", BOND_DIAG_DR: "DIAG_DR", BOND_DIAG_UR: "DIAG_UR"}
+
+# ---------------------------------------------------------------- spin-1/2 operators
+SZ = np.array([[0.5, 0.0], [0.0, -0.5]])
+SP = np.array([[0.0, 1.0], [0.0, 0.0]])  # S^+ |down> = |up>, basis (up, down)
+SM = SP.T.copy()
+
+
+def heisenberg_bond() -> np.ndarray:
+    """S_1 . S_2 = Sz Sz + (S+ S- + S- S+)/2 as a 4x4 real matrix (Eq. SSM, one term)."""
+    return np.kron(SZ, SZ) + 0.5 * (np.kron(SP, SM) + np.kron(SM, SP))
+
+
+def heisenberg_bond_rotated() -> np.ndarray:
+    """S_1 . S_2 after the sublattice rotation U = -i sigma_y on site 2.
+
+    -i sigma_y = [[0, -1], [1, 0]] is real; conjugating site 2 by it maps
+    (Sx, Sy, Sz) -> (-Sx, Sy, -Sz), so the bond becomes
+    -Sz Sz - (S+ S+ + S- S-)/2.  This is the input of the 1-site ansatz
+    (Sec. Outlook, local spin rotation on one sublattice).
+    """
+    U = np.array([[0.0, -1.0], [1.0, 0.0]])
+    W = np.kron(np.eye(2), U)
+    return W.T @ heisenberg_bond() @ W
+
+
+@dataclasses.dataclass
+class Term:
+    x: int
+    y: int
+    kind: int
+    coupling: float
+    h: np.ndarray  # d^2 x d^2
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    Lx: int
+    Ly: int
+    d: int
+    D: int
+    chi: int
+    n_iter: int
+    tensors: list  # Lx*Ly arrays [d, D, D, D, D], float64
+    terms: list    # list[Term]
+    precision: str = "fp64"
+
+    @property
+    def n_sites(self) -> int:
+        return self.Lx * self.Ly
+
+
+def random_site(seed: int, d: int, D: int, std: float | None = None, maxabs: bool = False,
+                signed: bool = False) -> np.ndarray:
+    """|N(0,1)| draw from ``np.random.default_rng(seed)``, scaled by ``std`` or to max-abs 1.
+
+    The absolute value is taken because the nested single-layer CTMRG does not
+    converge on sign-mixed random tensors (its cuts are not Hermitian; the
+    iteration is then chaotic), while the sublattice-rotated Heisenberg ground
+    state it is meant for is sign-free.  ``signed=True`` keeps the raw draw.
+    """
+    a = np.random.default_rng(seed).standard_normal((d, D, D, D, D))
+    if not signed:
+        a = np.abs(a)
+    if maxabs:
+        a = a / np.abs(a).max()
+    elif std is not None:
+        a = a * std
+    return a
+
+
+def heisenberg_terms_rotated(J: float = 1.0) -> list:
+    """1-site ansatz with sublattice rotation: one H and one V bond per site."""
+    h = heisenberg_bond_rotated()
+    return [Term(0, 0, BOND_H, J, h), Term(0, 0, BOND_V, J, h)]
+
+
+def shastry_sutherland_terms(J: float = 0.7, Jp: float = 1.0) -> list:
+    """Shastry-Sutherland model on a 2x2 cell [A B; C F] (Eq. SSM).
+
+    J on every nearest-neighbour bond (8 per cell), J' on the two dimer
+    diagonals per cell: A(0,0)-F(1,1) and B(1,0)-C(0,1) of the next cell up
+    and to the right, i.e. the DIAG_UR bond of the plaquette whose upper-left
+    site is (1, 1).
+    """
+    h = heisenberg_bond()
+    terms = []
+    for y in range(2):
+        for x in range(2):
+            terms.append(Term(x, y, BOND_H, J, h))
+            terms.append(Term(x, y, BOND_V, J, h))
+    terms.append(Term(0, 0, BOND_DIAG_DR, Jp, h))
+    terms.append(Term(1, 1, BOND_DIAG_UR, Jp, h))
+    return terms
+
+
+def config(name: str) -> Workload:
+    """The seeded workloads: shapes and distributions of the paper's runs.
+
+    heis_d2_chi8:  D=2, chi=8, 20 iterations, one tensor |N(0,1)| seed 0 / max-abs
+    heis_d4_chi32: D=4, chi=32, 40 iterations, |N(0,1)| seed 1, std 1/sqrt(2 D^4)
+    ss_d6_chi64:   Shastry-Sutherland J=0.7, J'=1, 2x2 cell, D=6, chi=64,
+                   50 iterations, seeds 2..5 (one per site), std 1/sqrt(2 D^4)
+    heis_d9_chi81: D=9, chi=81, 60 iterations, seed 6, std 1/sqrt(2 D^4)
+    """
+    d = 2
+    if name == "heis_d2_chi8":
+        D = 2
+        return Workload(name, 1, 1, d, D, 8, 20, [random_site(0, d, D, maxabs=True)], heisenberg_terms_rotated())
+    if name == "heis_d4_chi32":
+        D = 4
+        return Workload(name, 1, 1, d, D, 32, 40, [random_site(1, d, D, std=1 / np.sqrt(2 * D**4))],
+                        heisenberg_terms_rotated(), precision="tf32")
+    if name == "ss_d6_chi64":
+        D = 6
+        ts = [random_site(s, d, D, std=1 / np.sqrt(2 * D**4)) for s in (2, 3, 4, 5)]
+        return Workload(name, 2, 2, d, D, 64, 50, ts, shastry_sutherland_terms(), precision="bf16")
+    if name == "heis_d9_chi81":
+        D = 9
+        return Workload(name, 1, 1, d, D, 81, 60, [random_site(6, d, D, std=1 / np.sqrt(2 * D**4))],
+                        heisenberg_terms_rotated(), precision="bf16")
+    raise KeyError(name)
+
+
+def custom(Lx, Ly, D, chi, n_iter, seeds, terms, d=2, std=None, maxabs=False, name="custom") -> Workload:
+    """A workload of arbitrary size drawn the same way (used by scaled-down tests)."""
+    if std is None and not maxabs:
+        std = 1 / np.sqrt(2 * D**4)
+    ts = [random_site(s, d, D, std=std, maxabs=maxabs) for s in seeds]
+    assert len(ts) == Lx * Ly
+    return Workload(name, Lx, Ly, d, D, chi, n_iter, ts, terms)
+
+
+# --------------------------------------------------------------- special product states
+def neel_rotated_site(D: int = 1, d: int = 2) -> np.ndarray:
+    """D=1 rotated Neel state: A[s] = delta_{s, up} (ferromagnet after rotation)."""
+    a = np.zeros((d, D, D, D, D))
+    a[0, 0, 0, 0, 0] = 1.0
+    return a
+
+
+def product_site(v) -> np.ndarray:
+    """D=1 product state A[s] = v_s."""
+    v = np.asarray(v, dtype=np.float64)
+    return v.reshape(-1, 1, 1, 1, 1).copy()
+
+
+def dimer_singlet_sites() -> list:
+    """Exact D=2 PEPS of the Shastry-Sutherland dimer-singlet product state.
+
+    Cell [A B; C F].  Every J' singlet is routed along an L-shaped path through
+    one intermediate site; unused virtual legs carry index 0.  With the
+    singlet matrix eps = [[0, 1], [-1, 0]] / sqrt(2):
+      A[s; l, u, d] = delta_{l u} delta_{s d}      (r = 0)
+      B[s; r]       = delta_{s r}                  (l = u = d = 0)
+      C[s; u, r, d] = delta_{u r} eps_{d s}        (l = 0)
+      F[s; l]       = eps_{l s}                    (u = r = d = 0)
+    The A-F singlet runs A -down-> C -right-> F; the B-C' singlet (C' in the
+    cell up and to the right) runs B -right-> A' -up-> C'.
+    """
+    D, d = 2, 2
+    eps = np.array([[0.0, 1.0], [-1.0, 0.0]]) / np.sqrt(2.0)
+    A = np.zeros((d, D, D, D, D))
+    B = np.zeros((d, D, D, D, D))
+    C = np.zeros((d, D, D, D, D))
+    F = np.zeros((d, D, D, D, D))
+    for s in range(d):
+        for k in range(D):
+            A[s, k, k, 0, s] = 1.0          # l = u = k, d = s
+            B[s, 0, 0, s, 0] = 1.0          # r = s
+            for t in range(D):
+                C[s, 0, k, k, t] = eps[t, s]  # u = r = k, d = t
+            F[s, k, 0, 0, 0] = eps[k, s]    # l = k
+    return [A, B, C, F]
+
+
+# --------------------------------------------------------------- nested layout and initial environment
+ENV_SLOTS = ("C_ul", "T_u", "C_ur", "T_r", "C_dr", "T_d", "C_dl", "T_l")
+
+
+def nested_leg_dims(i: int, j: int, D: int, d: int):
+    """(left, up, right, down) bond dimensions of nested site (row i, col j).
+
+    Ket at (even, even): right leg fused with sigma (D d).  Y at (even, odd):
+    left and down legs D d.  X at (odd, even): all D.  Bra at (odd, odd): up
+    leg fused with sigma (D d).
+    """
+    Dd = D * d
+    if i % 2 == 0 and j % 2 == 0:
+        return (D, D, Dd, D)
+    if i % 2 == 0:
+        return (Dd, D, D, Dd)
+    if j % 2 == 0:
+        return (D, D, D, D)
+    return (D, Dd, D, D)
+
+
+def env_shapes(Lx: int, Ly: int, D: int, d: int, chi: int):
+    """Shapes of the 8 environment tensors of every nested site, row-major over the
+    2Ly x 2Lx nested cell.  Ring convention (clockwise around the site):
+    C: [prev, next], T: [prev, in, next], slots in ENV_SLOTS order, where
+    C_ul = [down, right], T_u = [left, in, right], C_ur = [left, down],
+    T_r = [up, in, down], C_dr = [up, left], T_d = [right, in, left],
+    C_dl = [right, up], T_l = [down, in, up]."""
+    out = []
+    for i in range(2 * Ly):
+        for j in range(2 * Lx):
+            l, u, r, dn = nested_leg_dims(i, j, D, d)
+            out.append([(chi, chi), (chi, u, chi), (chi, chi), (chi, r, chi),
+                        (chi, chi), (chi, dn, chi), (chi, chi), (chi, l, chi)])
+    return out
+
+
+def initial_environment(w, seed: int = 12345):
+    """Seeded positive random initial environment: every entry U(0,1).
+
+    Drawn site by site (row-major), slot by slot (ENV_SLOTS order), each
+    array in C order, from one ``np.random.default_rng(seed)`` stream.
+    """
+    rng = np.random.default_rng(seed)
+    return [[rng.random(shp) for shp in site] for site in env_shapes(w.Lx, w.Ly, w.D, w.d, w.chi)]

@@ -1,0 +1,147 @@
+/*
+ * libctm -- nested single-layer CTMRG energy and gradient on one GB300 GPU.
+ *
+ * C ABI.  Plain pointers and sizes only.  Every entry point returns an int
+ * status: CTM_OK (0) or one of the CTM_ERR_* codes below.  No C++ exception
+ * crosses this boundary.  A failed call leaves the handle valid; the next
+ * ctm_init clears its error state.
+ *
+ * The method (arXiv:2512.14414, Sec. SLF):
+ *   E(X) = <Psi|H|Psi> / <Psi|Psi>                                   (Eq. ExpH)
+ * evaluated on the nested single-layer network in which ket A and bra A* are
+ * separate sites, joined by the crossing tensors X and Y (Eq. XY), contracted
+ * by multisite CTMRG (Fig. 3) with projectors from QR + SVD (Eqs. PQ, QRSVD);
+ * the gradient dE/dX is reverse mode through every CTMRG iteration (Eq. AD).
+ *
+ * Layouts (all row-major, C order):
+ *   site tensors   A: batch x (Lx*Ly) x [d][D][D][D][D]  = A[s][l][u][r][d];
+ *                  PEPS site (x, y) at index y*Lx + x.
+ *   environment    per nested site (row-major over the 2Ly x 2Lx nested cell),
+ *                  8 tensors in the order C_ul, T_u, C_ur, T_r, C_dr, T_d,
+ *                  C_dl, T_l, each in the ring convention (legs listed
+ *                  clockwise around the site): C = [prev][next],
+ *                  T = [prev][in][next], with
+ *                    C_ul [down][right]   T_u [left][in][right]
+ *                    C_ur [left][down]    T_r [up][in][down]
+ *                    C_dr [up][left]      T_d [right][in][left]
+ *                    C_dl [right][up]     T_l [down][in][up].
+ *                  "in" is the leg of the site on that side; its size is D,
+ *                  or D*d (index k*d + s) for the ket's right leg, the
+ *                  bra's up leg and Y's left and down legs.
+ *   bond operator  h: d^2 x d^2, row (s1 s2), column (s1' s2'), host memory.
+ *
+ * Ownership: the caller owns every pointer it passes; the library copies
+ * what it needs at the call and never frees caller memory.  Device pointers
+ * must be device memory of the current device; all work is enqueued on the
+ * given stream, and results written to device pointers are valid when that
+ * stream reaches the point after the call.  Host output pointers (delta,
+ * iteration counts, energies marked host) are valid on return (the call
+ * synchronises the stream for them).
+ *
+ * Threads: one handle per host thread; handles share nothing.
+ */
+#ifndef CTM_H
+#define CTM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ctm_handle ctm_handle;
+
+enum {
+  CTM_OK = 0,
+  CTM_ERR_INVALID_ARG = 1,  /* bad size, null pointer, unsupported combination */
+  CTM_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  CTM_ERR_OOM = 3,          /* device allocation failed */
+  CTM_ERR_NONFINITE = 4,    /* NaN or Inf in a spectrum or in the energy */
+  CTM_ERR_SVD_NOCONV = 5,   /* Jacobi SVD hit its sweep limit */
+  CTM_ERR_DEGENERATE = 6,   /* all singular values of a bond density matrix are zero */
+  CTM_ERR_TIMEOUT = 7,      /* a bounded device-side wait ran out */
+  CTM_ERR_STATE = 8         /* call out of order (e.g. ctm_step before ctm_init) */
+};
+
+/* Arithmetic of the contractions.  QR, SVD, projectors, their adjoints and
+ * the final trace/normalisation of the energy are FP64 in every mode. */
+typedef enum {
+  CTM_FP64 = 0,    /* FP64 everywhere */
+  CTM_TF32 = 1,    /* contractions TF32 x TF32 -> FP32 on the tensor cores */
+  CTM_BF16 = 2,    /* contractions BF16 x BF16 -> FP32 on the tensor cores */
+  CTM_TF32X3 = 3,  /* error-compensated TF32 (hi*hi + hi*lo + lo*hi) */
+  CTM_BF16X3 = 4   /* error-compensated BF16 */
+} ctm_precision;
+
+/* Bond kinds, relative to PEPS site (x, y):
+ *   H: (x,y)-(x+1,y)   V: (x,y)-(x,y+1)
+ *   DIAG_DR: (x,y)-(x+1,y+1)   DIAG_UR: (x+1,y)-(x,y+1)  (first site listed first) */
+typedef enum { CTM_BOND_H = 0, CTM_BOND_V = 1, CTM_BOND_DIAG_DR = 2, CTM_BOND_DIAG_UR = 3 } ctm_bond_kind;
+
+typedef struct {
+  int x, y;              /* PEPS site of the bond, 0 <= x < Lx, 0 <= y < Ly */
+  int kind;              /* ctm_bond_kind */
+  double coupling;       /* J of this term */
+  const double* h;       /* d^2 x d^2 bond operator, host memory, copied at ctm_create */
+} ctm_term;
+
+typedef struct {
+  int Lx, Ly;            /* PEPS unit cell; nested cell is 2Ly x 2Lx */
+  int d, D, chi;         /* physical, bond and environment dimensions */
+  int precision;         /* ctm_precision */
+  int n_terms;
+  const ctm_term* terms; /* Hamiltonian: sum of coupling * h over the listed bonds */
+  double svd_cutoff_rel; /* projector pseudo-inverse cutoff s_k <= cut*s_1 -> 0; <=0 means 1e-6 */
+  double svd_adjoint_eps;/* Lorentzian broadening of 1/(s_j^2-s_i^2), relative to s_1^4; <0 means 1e-30 */
+  int max_iter;          /* upper bound on iterations stored for the gradient (sizes the factor store) */
+} ctm_desc;
+
+/* Create a handle for one problem size (Eq. PEPS cell, D, chi, terms).
+ * Allocates the device state lazily on first use.  *out is set on success. */
+int ctm_create(const ctm_desc* desc, ctm_handle** out);
+
+/* Load the site tensors and the initial environment.
+ *   A        : device, FP64, layout above (Lx*Ly tensors).
+ *   env0     : device, FP64, concatenation of all nested sites' 8 tensors
+ *              (layout above); NULL keeps the environment already in the
+ *              handle (e.g. from ctm_set_env).
+ * Resets the iteration counter and the stored projector factors. */
+int ctm_init(ctm_handle* h, const double* A, const double* env0, void* stream);
+
+/* Run n_iter CTMRG iterations (left, right, up, down moves; Sec. SLF) from
+ * the current environment.  Records the projector factors so that a
+ * following ctm_grad can differentiate them.  If delta_host is non-NULL it
+ * receives the spectrum change of the last iteration:
+ * max over projector pairs of ||s~/|s~|_1 - s~_prev/|s~_prev|_1||_inf. */
+int ctm_step(ctm_handle* h, int n_iter, double* delta_host, void* stream);
+
+/* Energy per PEPS site of the current environment (Eq. ExpH with the
+ * impurity reduced density matrices).  e_site_dev: device, 1 double.
+ * e_bonds_dev: device, n_terms doubles (per-term Tr(rho h)/Tr(rho)), or NULL. */
+int ctm_energy(ctm_handle* h, double* e_site_dev, double* e_bonds_dev, void* stream);
+
+/* Energy and its gradient with respect to A (Eq. AD): re-initialises from the
+ * environment given at ctm_init, runs n_iter iterations, evaluates the
+ * energy, then back-propagates through the energy and every iteration
+ * (recomputing each iteration from its stored environment).
+ *   e_site_dev : device, 1 double.   dA_dev : device, FP64, layout of A. */
+int ctm_grad(ctm_handle* h, int n_iter, double* e_site_dev, double* dA_dev, void* stream);
+
+/* Copy the current environment out / in (FP64, layout above). */
+int ctm_get_env(ctm_handle* h, double* env_dev, void* stream);
+int ctm_set_env(ctm_handle* h, const double* env_dev, void* stream);
+
+/* Number of doubles of the environment buffer (sum over nested sites and slots). */
+int64_t ctm_env_numel(const ctm_handle* h);
+
+/* Launch counters (kernels enqueued by this handle since creation). */
+int64_t ctm_kernel_launches(const ctm_handle* h);
+
+int ctm_destroy(ctm_handle* h);
+const char* ctm_error_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTM_H */

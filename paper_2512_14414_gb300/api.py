@@ -1,0 +1,121 @@
+"""Python binding of libctm: the same calls as include/ctm.h on torch device memory.
+
+Every step of the path runs inside libctm's CUDA kernels; this module only
+marshals arguments (device pointers of torch tensors, the current stream).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+class CTMError(RuntimeError):
+    def __init__(self, status, where):
+        lib = _lib.load()
+        super().__init__(f"{where}: {lib.ctm_error_string(status).decode()} (status {status})")
+        self.status = status
+
+
+def _check(status, where):
+    if status != 0:
+        raise CTMError(status, where)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class CTM:
+    """One problem size: PEPS cell Lx x Ly, d, D, chi, precision, Hamiltonian terms.
+
+    ``terms``: iterable of (x, y, kind, coupling, h) with h a d^2 x d^2 array.
+    """
+
+    def __init__(self, Lx, Ly, d, D, chi, terms, precision="fp64", cutoff=1e-6, adjoint_eps=1e-30):
+        self.lib = _lib.load()
+        self.Lx, self.Ly, self.d, self.D, self.chi = Lx, Ly, d, D, chi
+        self.precision = precision
+        self._h = [np.ascontiguousarray(np.asarray(t[4], dtype=np.float64)) for t in terms]
+        arr = (_lib.CtmTerm * len(self._h))()
+        for k, t in enumerate(terms):
+            arr[k].x, arr[k].y, arr[k].kind, arr[k].coupling = int(t[0]), int(t[1]), int(t[2]), float(t[3])
+            arr[k].h = self._h[k].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        desc = _lib.CtmDesc(Lx, Ly, d, D, chi, _lib.PRECISIONS[precision], len(self._h), arr, cutoff, adjoint_eps, 0)
+        self._terms = arr
+        h = ctypes.c_void_p()
+        _check(self.lib.ctm_create(ctypes.byref(desc), ctypes.byref(h)), "ctm_create")
+        self.handle = h
+        self.n_terms = len(self._h)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            self.lib.ctm_destroy(self.handle)
+            self.handle = None
+
+    @property
+    def env_numel(self):
+        return int(self.lib.ctm_env_numel(self.handle))
+
+    @property
+    def kernel_launches(self):
+        return int(self.lib.ctm_kernel_launches(self.handle))
+
+    def init(self, A, env0=None):
+        """A: cuda float64 [Lx*Ly, d, D, D, D, D]; env0: cuda float64 flat ring-layout environment."""
+        assert A.is_cuda and A.dtype == torch.float64 and A.is_contiguous()
+        if env0 is not None:
+            assert env0.is_cuda and env0.dtype == torch.float64 and env0.numel() == self.env_numel
+        _check(self.lib.ctm_init(self.handle, _ptr(A), _ptr(env0), _stream()), "ctm_init")
+
+    def step(self, n_iter):
+        delta = ctypes.c_double(-1.0)
+        _check(self.lib.ctm_step(self.handle, int(n_iter), ctypes.byref(delta), _stream()), "ctm_step")
+        return delta.value
+
+    def energy(self, per_bond=False):
+        e = torch.empty(1, dtype=torch.float64, device="cuda")
+        eb = torch.empty(self.n_terms, dtype=torch.float64, device="cuda") if per_bond else None
+        _check(self.lib.ctm_energy(self.handle, _ptr(e), _ptr(eb), _stream()), "ctm_energy")
+        return (e, eb) if per_bond else e
+
+    def grad(self, n_iter, dA=None, e=None):
+        nA = self.Lx * self.Ly * self.d * self.D ** 4
+        dA = dA if dA is not None else torch.empty(self.Lx * self.Ly, self.d, self.D, self.D, self.D, self.D,
+                                                  dtype=torch.float64, device="cuda")
+        e = e if e is not None else torch.empty(1, dtype=torch.float64, device="cuda")
+        assert dA.numel() == nA
+        _check(self.lib.ctm_grad(self.handle, int(n_iter), _ptr(e), _ptr(dA), _stream()), "ctm_grad")
+        return e, dA
+
+    def get_env(self):
+        out = torch.empty(self.env_numel, dtype=torch.float64, device="cuda")
+        _check(self.lib.ctm_get_env(self.handle, _ptr(out), _stream()), "ctm_get_env")
+        return out
+
+    def set_env(self, env):
+        assert env.is_cuda and env.dtype == torch.float64 and env.numel() == self.env_numel
+        _check(self.lib.ctm_set_env(self.handle, _ptr(env), _stream()), "ctm_set_env")
+
+
+class CTMEnergy(torch.autograd.Function):
+    """E(A) after n_iter CTMRG iterations from env0; backward returns dE/dA from ctm_grad."""
+
+    @staticmethod
+    def forward(ctx, A, ctm, env0, n_iter):
+        ctm.init(A.detach().contiguous(), env0)
+        e, dA = ctm.grad(n_iter)
+        ctx.save_for_backward(dA)
+        return e[0].clone()
+
+    @staticmethod
+    def backward(ctx, g):
+        (dA,) = ctx.saved_tensors
+        return g * dA, None, None, None

@@ -1,0 +1,1171 @@
+// The nested single-layer CTMRG of arXiv:2512.14414 (Sec. SLF) on the engine of engine.h,
+// and the C ABI of include/ctm.h.
+//
+// Network.  Per PEPS site the nested cell is [A  Y; X  A*] (ket at even row /
+// even column, Y at even/odd, X at odd/even, bra at odd/odd; Fig. 2(c)).  The
+// crossing tensors X and Y (Eq. XY) are never stored: they only identify
+// labels.  X passes its left label to its right and its up label to its
+// down; Y passes (i, s) on its left to i on its right and s down, and its up
+// label k to its down leg (k, s).  So the ket's right leg is (r, s) and the
+// bra's up leg is (u, s), the two D*d bonds of the paper's footnote on bond
+// dimensions; every contraction below is a pairwise labelled contraction
+// (permute + batched GEMM) over the stored tensors A and the environment.
+//
+// CTMRG (Fig. 3).  Every nested site owns 4 corners and 4 edges.  A left move
+// runs over the columns j in order: for every row i the 2x2 cluster of sites
+// (i..i+1, j..j+1) with their environments gives the upper half N (rows: the
+// open right cut, columns: the left cut where P Q^t is inserted) and the lower
+// half S; the projectors of all rows come first (Eqs. PQ, QRSVD), then every
+// row absorbs column j into the left corner, edge and corner of (i, j+1).  The
+// right, up and down moves are left moves in the frame rotated by 180, 90 and
+// 270 degrees (counterclockwise); a rotation by q maps frame leg f to actual
+// leg (f + q) mod 4 (order left, up, right, down) and frame slot k to actual
+// slot (k + 2q) mod 8 (ring order C_ul, T_u, C_ur, T_r, C_dr, T_d, C_dl, T_l).
+//
+// Projectors.  With rho = N S^t, QR + SVD give P = S^t V' L~^{-1/2} and
+// Q = N^t U' L~^{-1/2} where U' L V'^t is the thin SVD of rho: for a tall N
+// (more right-cut rows than left-cut columns) U' = Q_n U, V' = Q_s V with
+// R_n R_s^t = U L V^t (Householder QR); otherwise Q_n is square and the SVD
+// is taken of rho itself, which is the same matrix up to that rotation.
+// L~^{-1/2} := 0 below cutoff * L_1.  The reverse mode is the adjoint of the
+// thin SVD of rho over its numerically non-zero singular values with the
+// Lorentzian-broadened 1/(s_j^2 - s_i^2) (no inverse of R is ever formed).
+//
+// Gradient.  Forward iterations keep no tape: they store the environment at
+// the start of every iteration and the factors U', V', L of every projector
+// pair.  The backward pass recomputes one iteration at a time from its stored
+// environment, taking P and Q from the stored factors (bit-identical to the
+// forward), and back-propagates through it (Eq. AD).
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+
+namespace ctm {
+namespace {
+
+constexpr double kRankTol = 1e-13;
+constexpr int kMaxSweeps = 60;
+
+enum Kind { KET = 0, YS = 1, XS = 2, BRA = 3 };
+inline int kind_of(int i, int j) { return (i % 2 == 0) ? ((j % 2 == 0) ? KET : YS) : ((j % 2 == 0) ? XS : BRA); }
+
+// ------------------------------------------------------------------ labels with identification
+struct Net {
+  std::vector<int> par;
+  std::vector<int64_t> dim;
+  int make(int64_t d) {
+    par.push_back((int)par.size());
+    dim.push_back(d);
+    return (int)par.size() - 1;
+  }
+  int find(int x) {
+    while (par[x] != x) x = par[x] = par[par[x]];
+    return x;
+  }
+  void unify(int a, int b) {
+    a = find(a);
+    b = find(b);
+    CTM_CHECK(dim[a] == dim[b], CTM_ERR_INVALID_ARG, "bond dimension mismatch in network");
+    if (a != b) par[b] = a;
+  }
+  Labels res(const Labels& l) {
+    Labels r;
+    for (int x : l) r.push_back(find(x));
+    return r;
+  }
+};
+
+// A nested site placed in a network: its four legs (actual order L, U, R, D) as label lists.
+struct Pos {
+  int site = 0, kind = 0, peps = 0, q = 0;
+  std::array<Labels, 4> leg;
+  Labels tl;          // labels of the stored tensor A[s][l][u][r][d] (ket/bra only)
+  int s_ket = -1, s_bra = -1;  // open physical labels of an impurity Y
+  const Labels& frame(int f) const { return leg[(f + q) % 4]; }
+};
+
+struct Item {
+  Tensor t;
+  Labels l;
+};
+
+}  // namespace
+}  // namespace ctm
+
+// ==================================================================== handle
+struct ctm_handle {
+  ctm_desc d{};
+  struct TermH {
+    int x, y, kind;
+    double coup;
+    std::vector<double> h;
+  };
+  std::vector<TermH> terms;
+  int R = 0, C = 0, nsites = 0;
+  ctm::DType edt = ctm::F64;
+  double cut = 1e-6, eps = 1e-30;
+  int64_t launches = 0;
+  cudaStream_t st = nullptr;
+  std::unique_ptr<ctm::Arena> persist, tape, store;
+  std::unique_ptr<ctm::Engine> eng;
+  bool dev_ready = false, inited = false;
+  // persistent device state
+  ctm::Tensor A64, Amode;                          // site tensors
+  std::vector<std::array<ctm::Tensor, 8>> slots;   // environment slot buffers (edt)
+  std::vector<std::array<ctm::Tensor, 8>> env;     // current environment values
+  std::vector<std::array<ctm::Tensor, 8>> denv;    // environment cotangents (edt)
+  double* env0 = nullptr;                          // FP64 copy of the initial environment
+  std::vector<std::vector<std::array<ctm::Tensor, 8>>> ckpt;  // environment at the start of each iteration
+  struct Fac {
+    double *U = nullptr, *V = nullptr, *lam = nullptr;
+    int64_t n_r = 0;
+    int r = 0;
+  };
+  std::vector<std::vector<Fac>> fac;  // [iteration][projector pair]
+  int iters_done = 0;
+  int* dstatus = nullptr;
+  int* dsweeps = nullptr;
+  double* dscal = nullptr;  // [0] delta
+  double *hs = nullptr, *coup = nullptr;
+  std::string last_error;
+  // replay state of the current iteration (backward recompute)
+  bool replay = false;
+  int cur_iter = 0, cur_pair = 0;
+};
+
+namespace ctm {
+namespace {
+
+// ------------------------------------------------------------------ geometry helpers
+inline void to_actual(int q, int R, int C, int fi, int fj, int& i, int& j) {
+  switch (q & 3) {
+    case 0: i = fi; j = fj; break;
+    case 1: i = fj; j = C - 1 - fi; break;
+    case 2: i = R - 1 - fi; j = C - 1 - fj; break;
+    default: i = R - 1 - fj; j = fi; break;
+  }
+}
+
+inline int mod(int a, int n) { return ((a % n) + n) % n; }
+
+struct Frame {
+  ctm_handle* h;
+  int q, FR, FC;
+  Frame(ctm_handle* hh, int qq) : h(hh), q(qq) {
+    FR = (q % 2 == 0) ? h->R : h->C;
+    FC = (q % 2 == 0) ? h->C : h->R;
+  }
+  int site(int fi, int fj) const {
+    int i, j;
+    to_actual(q, h->R, h->C, mod(fi, FR), mod(fj, FC), i, j);
+    return i * h->C + j;
+  }
+  int slot(int fk) const { return (fk + 2 * q) % 8; }
+  Tensor& env(int s, int fk) const { return h->env[s][slot(fk)]; }
+};
+
+// elementary dims of the actual legs of a nested site
+std::array<std::vector<int64_t>, 4> leg_dims(int kind, int64_t D, int64_t d) {
+  std::array<std::vector<int64_t>, 4> r;
+  for (auto& x : r) x = {D};
+  if (kind == KET) r[2] = {D, d};
+  if (kind == YS) r[0] = {D, d}, r[3] = {D, d};
+  if (kind == BRA) r[1] = {D, d};
+  return r;
+}
+
+Pos make_pos(ctm_handle* h, Net& net, int site, int q, bool impurity) {
+  Pos p;
+  p.site = site;
+  p.q = q;
+  int i = site / h->C, j = site % h->C;
+  p.kind = kind_of(i, j);
+  p.peps = (i / 2) * h->d.Lx + (j / 2);
+  const int64_t D = h->d.D, d = h->d.d;
+  switch (p.kind) {
+    case KET: {
+      int s = net.make(d), a = net.make(D), b = net.make(D), c = net.make(D), e = net.make(D);
+      p.leg = {Labels{a}, Labels{b}, Labels{c, s}, Labels{e}};
+      p.tl = {s, a, b, c, e};
+      break;
+    }
+    case BRA: {
+      int s = net.make(d), a = net.make(D), b = net.make(D), c = net.make(D), e = net.make(D);
+      p.leg = {Labels{a}, Labels{b, s}, Labels{c}, Labels{e}};
+      p.tl = {s, a, b, c, e};
+      break;
+    }
+    case XS: {
+      int a = net.make(D), b = net.make(D);
+      p.leg = {Labels{a}, Labels{b}, Labels{a}, Labels{b}};
+      break;
+    }
+    default: {
+      int a = net.make(D), b = net.make(D);
+      if (impurity) {
+        int s1 = net.make(d), s2 = net.make(d);
+        p.leg = {Labels{a, s1}, Labels{b}, Labels{a}, Labels{b, s2}};
+        p.s_ket = s1;
+        p.s_bra = s2;
+      } else {
+        int s = net.make(d);
+        p.leg = {Labels{a, s}, Labels{b}, Labels{a}, Labels{b, s}};
+      }
+    }
+  }
+  return p;
+}
+
+// identify the frame leg fa of A with the frame leg fb of B
+void bond(Net& net, const Pos& A, int fa, const Pos& B, int fb) {
+  const Labels& x = A.frame(fa);
+  const Labels& y = B.frame(fb);
+  CTM_CHECK(x.size() == y.size(), CTM_ERR_INVALID_ARG, "bond structure mismatch");
+  for (size_t k = 0; k < x.size(); ++k) net.unify(x[k], y[k]);
+}
+
+enum { FL = 0, FU = 1, FR = 2, FD = 3 };
+enum { S_CUL = 0, S_TU = 1, S_CUR = 2, S_TR = 3, S_CDR = 4, S_TD = 5, S_CDL = 6, S_TL = 7 };
+
+Labels cat(std::initializer_list<Labels> ls) {
+  Labels r;
+  for (auto& l : ls) r.insert(r.end(), l.begin(), l.end());
+  return r;
+}
+
+Labels natural_out(const Labels& a, const Labels& b) {
+  Labels r;
+  for (int x : a)
+    if (std::find(b.begin(), b.end(), x) == b.end()) r.push_back(x);
+  for (int x : b)
+    if (std::find(a.begin(), a.end(), x) == a.end()) r.push_back(x);
+  return r;
+}
+
+int64_t numel_of(const Labels& l, Net& net) {
+  int64_t n = 1;
+  for (int x : l) n *= net.dim[x];
+  return n;
+}
+
+// Greedy pairwise contraction: always the connected pair with the smallest result.
+Item contract_greedy(Engine& E, Net& net, std::vector<Item> items, const Labels* out = nullptr) {
+  CTM_CHECK(!items.empty(), CTM_ERR_INVALID_ARG, "empty contraction");
+  while (items.size() > 1) {
+    int bp = -1, bq = -1;
+    int64_t bsize = 0, bcost = 0;
+    for (size_t p = 0; p < items.size(); ++p)
+      for (size_t q = p + 1; q < items.size(); ++q) {
+        Labels o = natural_out(items[p].l, items[q].l);
+        size_t shared = items[p].l.size() + items[q].l.size() - o.size();
+        if (shared == 0) continue;
+        int64_t size = numel_of(o, net);
+        int64_t cost = size;
+        for (int x : items[p].l)
+          if (std::find(items[q].l.begin(), items[q].l.end(), x) != items[q].l.end()) cost *= net.dim[x];
+        if (bp < 0 || size < bsize || (size == bsize && cost < bcost)) {
+          bp = (int)p;
+          bq = (int)q;
+          bsize = size;
+          bcost = cost;
+        }
+      }
+    if (bp < 0) {  // no connected pair left: outer product of the first two
+      bp = 0;
+      bq = 1;
+    }
+    Labels o = natural_out(items[bp].l, items[bq].l);
+    if (items.size() == 2 && out) o = *out;
+    Item r{E.einsum(items[bp].t, items[bp].l, items[bq].t, items[bq].l, o), o};
+    std::vector<Item> nx;
+    for (size_t k = 0; k < items.size(); ++k)
+      if ((int)k != bp && (int)k != bq) nx.push_back(items[k]);
+    nx.push_back(r);
+    items.swap(nx);
+  }
+  if (out && items[0].l != *out) {
+    // single item whose order differs: permute
+    std::vector<int> perm;
+    for (int x : *out) perm.push_back((int)(std::find(items[0].l.begin(), items[0].l.end(), x) - items[0].l.begin()));
+    items[0].t = E.permute(items[0].t, perm);
+    items[0].l = *out;
+  }
+  return items[0];
+}
+
+void sync_status(ctm_handle* h) {
+  int s = 0;
+  CTM_CUDA(cudaMemcpyAsync(&s, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CTM_CUDA(cudaStreamSynchronize(h->st));
+  if (s) {
+    CTM_CUDA(cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->st));
+    if (s & DEV_TIMEOUT) throw Error(CTM_ERR_TIMEOUT, "device wait timed out");
+    if (s & DEV_SVD_NOCONV) throw Error(CTM_ERR_SVD_NOCONV, "Jacobi SVD did not converge");
+    if (s & DEV_NONFINITE) throw Error(CTM_ERR_NONFINITE, "non-finite value in spectrum or energy");
+    if (s & DEV_DEGENERATE) throw Error(CTM_ERR_DEGENERATE, "all singular values zero");
+  }
+}
+
+}  // namespace
+}  // namespace ctm
+
+using namespace ctm;
+
+// ==================================================================== per-site tensors of A
+// Amode is one buffer of Lx*Ly site tensors; a leaf per site lets einsum accumulate each
+// site's gradient into its own sub-buffer.
+namespace ctm {
+namespace {
+
+struct SiteLeaves {
+  std::vector<Tensor> t;  // one per PEPS site (views into Amode)
+};
+
+SiteLeaves site_views(ctm_handle* h, bool leaves) {
+  SiteLeaves s;
+  int64_t per = (int64_t)h->d.d * h->d.D * h->d.D * h->d.D * h->d.D;
+  for (int p = 0; p < h->d.Lx * h->d.Ly; ++p) {
+    Tensor a;
+    a.dt = h->Amode.dt;
+    a.p = (char*)h->Amode.p + per * p * dtype_size(a.dt);
+    a.dims = {h->d.d, h->d.D, h->d.D, h->d.D, h->d.D};
+    s.t.push_back(leaves ? h->eng->leaf(a) : a);
+  }
+  return s;
+}
+
+thread_local SiteLeaves* g_sites = nullptr;
+
+void push_site(std::vector<Item>& v, Net& net, const Pos& p) {
+  if (p.kind == KET || p.kind == BRA) v.push_back({g_sites->t[p.peps], net.res(p.tl)});
+}
+
+Item env_item(const Frame& F, Net& net, int s, int fk, const Labels& prev, const Labels& in, const Labels& next) {
+  Tensor t = F.env(s, fk);
+  return {t, net.res(cat({prev, in, next}))};
+}
+
+// ------------------------------------------------------------------ projector op
+struct PairIn {
+  Tensor N, S;          // edt, [right cut..., left cut...]
+  int64_t n_r, n_l;
+  std::vector<int64_t> pdims, qdims;  // dims of P and Q tensors [chi, b..., chi]
+};
+
+void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, std::vector<Tensor>& Q) {
+  Engine& E = *h->eng;
+  cudaStream_t st = h->st;
+  const int chi = h->d.chi;
+  const int nb = (int)in.size();
+  P.assign(nb, Tensor());
+  Q.assign(nb, Tensor());
+  // per-row FP64 operands
+  std::vector<Tensor> N64(nb), S64(nb);
+  for (int b = 0; b < nb; ++b) {
+    Tensor n2 = in[b].N, s2 = in[b].S;
+    n2.dims = {in[b].n_r, in[b].n_l};
+    s2.dims = {in[b].n_r, in[b].n_l};
+    N64[b] = (n2.dt == F64) ? n2 : E.cast(n2, F64);
+    S64[b] = (s2.dt == F64) ? s2 : E.cast(s2, F64);
+    N64[b].id = S64[b].id = -1;  // gradients are routed by hand below
+  }
+  int r = (int)std::min(in[0].n_r, in[0].n_l);
+  for (auto& x : in) CTM_CHECK(std::min(x.n_r, x.n_l) == r, CTM_ERR_INVALID_ARG, "projector rank size differs");
+  const int kept = std::min(chi, r);
+  auto& fac = h->fac[h->cur_iter];
+  if ((int)fac.size() < h->cur_pair + nb) fac.resize(h->cur_pair + nb);
+  std::vector<ctm_handle::Fac*> F(nb);
+  for (int b = 0; b < nb; ++b) {
+    F[b] = &fac[h->cur_pair + b];
+    if (!F[b]->U) {
+      F[b]->n_r = in[b].n_r;
+      F[b]->r = r;
+      F[b]->U = (double*)h->store->alloc(sizeof(double) * in[b].n_r * r);
+      F[b]->V = (double*)h->store->alloc(sizeof(double) * in[b].n_r * r);
+      F[b]->lam = (double*)h->store->alloc(sizeof(double) * r);
+    }
+  }
+  if (!h->replay) {
+    const int64_t rr = (int64_t)r * r;
+    double* W = (double*)E.arena().alloc(sizeof(double) * rr * nb);
+    double* Vw = (double*)E.arena().alloc(sizeof(double) * rr * nb);
+    double* lam = (double*)E.arena().alloc(sizeof(double) * r * nb);
+    double* Uo = (double*)E.arena().alloc(sizeof(double) * rr * nb);
+    double* Vo = (double*)E.arena().alloc(sizeof(double) * rr * nb);
+    std::vector<double*> Nc(nb, nullptr), Sc(nb, nullptr), tn(nb, nullptr), ts(nb, nullptr);
+    for (int b = 0; b < nb; ++b) {
+      const int64_t nr = in[b].n_r, nl = in[b].n_l;
+      GemmSpec g;
+      if (nr > nl) {  // tall: Householder QR of N and S (column-major copies)
+        Nc[b] = (double*)E.arena().alloc(sizeof(double) * nr * nl);
+        Sc[b] = (double*)E.arena().alloc(sizeof(double) * nr * nl);
+        tn[b] = (double*)E.arena().alloc(sizeof(double) * nl);
+        ts[b] = (double*)E.arena().alloc(sizeof(double) * nl);
+        PermSpec ps;
+        ps.rank = 2;
+        ps.out_dims[0] = nl;
+        ps.out_dims[1] = nr;
+        ps.in_stride[0] = 1;
+        ps.in_stride[1] = nl;
+        permute(N64[b].p, F64, Nc[b], F64, ps, false, 1.0, st);
+        permute(S64[b].p, F64, Sc[b], F64, ps, false, 1.0, st);
+        qr_householder(Nc[b], tn[b], 1, (int)nr, (int)nl, nr * nl, h->dstatus, st);
+        qr_householder(Sc[b], ts[b], 1, (int)nr, (int)nl, nr * nl, h->dstatus, st);
+        double* Rn = (double*)E.arena().alloc(sizeof(double) * nl * nl);
+        double* Rs = (double*)E.arena().alloc(sizeof(double) * nl * nl);
+        qr_extract_R(Nc[b], Rn, 1, (int)nr, (int)nl, nr * nl, st);
+        qr_extract_R(Sc[b], Rs, 1, (int)nr, (int)nl, nr * nl, st);
+        // W = (R_n R_s^t)^t = R_s R_n^t, i.e. M column-major
+        g.M = nl; g.N = nl; g.K = nl; g.transA = false; g.lda = nl; g.transB = true; g.ldb = nl; g.ldc = nl;
+        gemm_f64(Rs, Rn, W + b * rr, g, st);
+      } else {        // rho = N S^t is r x r: W = (N S^t)^t = S N^t
+        g.M = nr; g.N = nr; g.K = nl; g.transA = false; g.lda = nl; g.transB = true; g.ldb = nl; g.ldc = nr;
+        gemm_f64((const double*)S64[b].p, (const double*)N64[b].p, W + b * rr, g, st);
+      }
+    }
+    set_identity_colmajor(Vw, nb, r, st);
+    svd_jacobi(W, Vw, lam, Uo, Vo, nb, r, kMaxSweeps, h->dstatus, h->dsweeps, st);
+    for (int b = 0; b < nb; ++b) {
+      const int64_t nr = in[b].n_r, nl = in[b].n_l;
+      CTM_CUDA(cudaMemcpyAsync(F[b]->lam, lam + (int64_t)b * r, sizeof(double) * r, cudaMemcpyDeviceToDevice, st));
+      if (nr > nl) {
+        for (int side = 0; side < 2; ++side) {
+          double* X = (double*)E.arena().alloc(sizeof(double) * nr * r);
+          embed_transpose((side ? Vo : Uo) + b * rr, r, X, nr, st);
+          qr_apply_Q(side ? Sc[b] : Nc[b], side ? ts[b] : tn[b], X, 1, (int)nr, (int)nl, r, nr * nl, nr * r, h->dstatus, st);
+          PermSpec ps;
+          ps.rank = 2;
+          ps.out_dims[0] = nr;
+          ps.out_dims[1] = r;
+          ps.in_stride[0] = 1;
+          ps.in_stride[1] = nr;
+          permute(X, F64, side ? F[b]->V : F[b]->U, F64, ps, false, 1.0, st);
+        }
+      } else {
+        CTM_CUDA(cudaMemcpyAsync(F[b]->U, Uo + b * rr, sizeof(double) * rr, cudaMemcpyDeviceToDevice, st));
+        CTM_CUDA(cudaMemcpyAsync(F[b]->V, Vo + b * rr, sizeof(double) * rr, cudaMemcpyDeviceToDevice, st));
+      }
+    }
+  }
+  // P = S^t V' L^-1/2, Q = N^t U' L^-1/2 (identical in forward and replay)
+  struct Saved {
+    double *inv, *sinv, *Wp, *Zp;
+  };
+  std::vector<Saved> sv(nb);
+  for (int b = 0; b < nb; ++b) {
+    const int64_t nr = in[b].n_r, nl = in[b].n_l;
+    Saved& s = sv[b];
+    s.inv = (double*)E.arena().alloc(sizeof(double) * kept);
+    s.sinv = (double*)E.arena().alloc(sizeof(double) * r);
+    s.Wp = (double*)E.arena().alloc(sizeof(double) * nr * kept);
+    s.Zp = (double*)E.arena().alloc(sizeof(double) * nr * kept);
+    proj_prepare(F[b]->lam, F[b]->U, F[b]->V, s.inv, s.sinv, 1, nr, r, kept, h->cut, kRankTol, h->dstatus, st);
+    scale_cols(F[b]->V, r, 0, s.inv, 0, s.Wp, 1, nr, kept, st);
+    scale_cols(F[b]->U, r, 0, s.inv, 0, s.Zp, 1, nr, kept, st);
+    Tensor P64 = E.zeros(F64, {nl, (int64_t)chi});
+    Tensor Q64 = E.zeros(F64, {nl, (int64_t)chi});
+    GemmSpec g;
+    g.M = nl; g.N = kept; g.K = nr; g.transA = true; g.lda = nl; g.transB = false; g.ldb = kept; g.ldc = chi;
+    gemm_f64((const double*)S64[b].p, s.Wp, (double*)P64.p, g, st);
+    gemm_f64((const double*)N64[b].p, s.Zp, (double*)Q64.p, g, st);
+    P64.dims = in[b].pdims;
+    Q64.dims = in[b].qdims;
+    P[b] = (h->edt == F64) ? P64 : E.cast(P64, h->edt);
+    Q[b] = (h->edt == F64) ? Q64 : E.cast(Q64, h->edt);
+    P[b].id = Q[b].id = -1;
+  }
+  h->cur_pair += nb;
+  if (!E.recording()) return;
+  // ---- reverse mode of (N, S) -> (P, Q)
+  bool any = false;
+  for (auto& x : in) any = any || x.N.id >= 0 || x.S.id >= 0;
+  if (!any) return;
+  std::vector<int> pid(nb), qid(nb);
+  for (int b = 0; b < nb; ++b) {
+    P[b].id = pid[b] = E.new_id(P[b]);
+    Q[b].id = qid[b] = E.new_id(Q[b]);
+  }
+  std::vector<ctm_handle::Fac> Fc(nb);
+  for (int b = 0; b < nb; ++b) Fc[b] = *F[b];
+  std::vector<PairIn> inc = in;
+  std::vector<Tensor> Pc = P, Qc = Q;
+  const double eps = h->eps;
+  const DType edt = h->edt;
+  ctm_handle* hh = h;
+  E.push([hh, &E, inc, N64, S64, Fc, sv, Pc, Qc, r, kept, chi, eps, edt, st]() {
+    for (size_t b = 0; b < inc.size(); ++b) {
+      void* gP = E.grad(Pc[b], false);
+      void* gQ = E.grad(Qc[b], false);
+      if (!gP && !gQ) continue;
+      const int64_t nr = inc[b].n_r, nl = inc[b].n_l;
+      auto A64 = [&](int64_t n) { return (double*)E.arena().alloc(sizeof(double) * std::max<int64_t>(n, 1)); };
+      double* dP = A64(nl * chi);
+      double* dQ = A64(nl * chi);
+      if (gP) cast(gP, edt, dP, F64, nl * chi, false, st); else fill(dP, F64, nl * chi, 0.0, st);
+      if (gQ) cast(gQ, edt, dQ, F64, nl * chi, false, st); else fill(dQ, F64, nl * chi, 0.0, st);
+      const double* N = (const double*)N64[b].p;
+      const double* S = (const double*)S64[b].p;
+      const double* U = Fc[b].U;
+      const double* V = Fc[b].V;
+      const double* lam = Fc[b].lam;
+      double* dN = A64(nr * nl);
+      double* dS = A64(nr * nl);
+      double* dW = A64(nr * kept);
+      double* dZ = A64(nr * kept);
+      GemmSpec g;
+      // dS = W dP^t, dN = Z dQ^t  (n_r x n_l, K = kept; dP has leading dimension chi)
+      g.M = nr; g.N = nl; g.K = kept; g.transA = false; g.lda = kept; g.transB = true; g.ldb = chi; g.ldc = nl;
+      gemm_f64(sv[b].Wp, dP, dS, g, st);
+      gemm_f64(sv[b].Zp, dQ, dN, g, st);
+      // dW = S dP, dZ = N dQ (n_r x kept)
+      g = GemmSpec();
+      g.M = nr; g.N = kept; g.K = nl; g.transA = false; g.lda = nl; g.transB = false; g.ldb = chi; g.ldc = kept;
+      gemm_f64(S, dP, dW, g, st);
+      gemm_f64(N, dQ, dZ, g, st);
+      double* dUk = A64(nr * kept);
+      double* dVk = A64(nr * kept);
+      double* dl = A64(kept);
+      scale_cols(dZ, kept, 0, sv[b].inv, 0, dUk, 1, nr, kept, st);
+      scale_cols(dW, kept, 0, sv[b].inv, 0, dVk, 1, nr, kept, st);
+      proj_dlam(dZ, U, dW, V, sv[b].inv, dl, 1, nr, r, kept, st);
+      double* Aa = A64((int64_t)r * kept);
+      double* Bb = A64((int64_t)r * kept);
+      g = GemmSpec();
+      g.M = r; g.N = kept; g.K = nr; g.transA = true; g.lda = r; g.transB = false; g.ldb = kept; g.ldc = kept;
+      gemm_f64(U, dUk, Aa, g, st);
+      gemm_f64(V, dVk, Bb, g, st);
+      double* core = A64((int64_t)r * r);
+      proj_core(Aa, Bb, lam, dl, core, 1, r, kept, kRankTol, eps, st);
+      double* Xu = A64(nr * kept);
+      double* Xv = A64(nr * kept);
+      g = GemmSpec();
+      g.M = nr; g.N = kept; g.K = r; g.lda = r; g.ldb = kept; g.ldc = kept;
+      gemm_f64(U, Aa, Xu, g, st);
+      gemm_f64(V, Bb, Xv, g, st);
+      double* Eu = A64(nr * kept);
+      double* Ev = A64(nr * kept);
+      proj_resid(dUk, Xu, sv[b].sinv, Eu, 1, nr, r, kept, st);
+      proj_resid(dVk, Xv, sv[b].sinv, Ev, 1, nr, r, kept, st);
+      // drho = U core V^t + Eu V_k^t + U_k Ev^t
+      double* T1 = A64(nr * r);
+      double* drho = A64(nr * nr);
+      g = GemmSpec();
+      g.M = nr; g.N = r; g.K = r; g.lda = r; g.ldb = r; g.ldc = r;
+      gemm_f64(U, core, T1, g, st);
+      g = GemmSpec();
+      g.M = nr; g.N = nr; g.K = r; g.lda = r; g.transB = true; g.ldb = r; g.ldc = nr;
+      gemm_f64(T1, V, drho, g, st);
+      g = GemmSpec();
+      g.M = nr; g.N = nr; g.K = kept; g.lda = kept; g.transB = true; g.ldb = r; g.ldc = nr; g.beta = 1.0;
+      gemm_f64(Eu, V, drho, g, st);
+      g = GemmSpec();
+      g.M = nr; g.N = nr; g.K = kept; g.lda = r; g.transB = true; g.ldb = kept; g.ldc = nr; g.beta = 1.0;
+      gemm_f64(U, Ev, drho, g, st);
+      // dN += drho S, dS += drho^t N
+      g = GemmSpec();
+      g.M = nr; g.N = nl; g.K = nr; g.lda = nr; g.ldb = nl; g.ldc = nl; g.beta = 1.0;
+      gemm_f64(drho, S, dN, g, st);
+      g.transA = true;
+      gemm_f64(drho, N, dS, g, st);
+      if (inc[b].N.id >= 0) cast(dN, F64, E.grad(inc[b].N), edt, nr * nl, true, st);
+      if (inc[b].S.id >= 0) cast(dS, F64, E.grad(inc[b].S), edt, nr * nl, true, st);
+    }
+  });
+}
+
+// ------------------------------------------------------------------ one left move (in frame q)
+void left_move(ctm_handle* h, int q) {
+  Engine& E = *h->eng;
+  Frame F(h, q);
+  const int64_t chi = h->d.chi;
+  for (int j = 0; j < F.FC; ++j) {
+    auto mark = h->tape->mark();
+    std::vector<PairIn> pin(F.FR);
+    for (int i = 0; i < F.FR; ++i) {
+      Net net;
+      int s00 = F.site(i, j), s01 = F.site(i, j + 1), s10 = F.site(i + 1, j), s11 = F.site(i + 1, j + 1);
+      Pos p00 = make_pos(h, net, s00, q, false), p01 = make_pos(h, net, s01, q, false);
+      Pos p10 = make_pos(h, net, s10, q, false), p11 = make_pos(h, net, s11, q, false);
+      bond(net, p00, FR, p01, FL);
+      bond(net, p10, FR, p11, FL);
+      bond(net, p01, FD, p11, FU);
+      int x1 = net.make(chi), x2 = net.make(chi), x3 = net.make(chi), x4 = net.make(chi), x5 = net.make(chi);
+      int cu = net.make(chi), cl = net.make(chi), cr = net.make(chi);
+      int y1 = net.make(chi), y2 = net.make(chi), y3 = net.make(chi), y4 = net.make(chi), y5 = net.make(chi);
+      std::vector<Item> gul, gur, gdl, gdr;
+      gul.push_back(env_item(F, net, s00, S_CUL, {x1}, {}, {x2}));
+      gul.push_back(env_item(F, net, s00, S_TU, {x2}, p00.frame(FU), {x3}));
+      gul.push_back(env_item(F, net, s00, S_TL, {cu}, p00.frame(FL), {x1}));
+      push_site(gul, net, p00);
+      gur.push_back(env_item(F, net, s01, S_TU, {x3}, p01.frame(FU), {x4}));
+      gur.push_back(env_item(F, net, s01, S_CUR, {x4}, {}, {x5}));
+      gur.push_back(env_item(F, net, s01, S_TR, {x5}, p01.frame(FR), {cr}));
+      push_site(gur, net, p01);
+      gdl.push_back(env_item(F, net, s10, S_TL, {y1}, p10.frame(FL), {cl}));
+      gdl.push_back(env_item(F, net, s10, S_CDL, {y2}, {}, {y1}));
+      gdl.push_back(env_item(F, net, s10, S_TD, {y3}, p10.frame(FD), {y2}));
+      push_site(gdl, net, p10);
+      gdr.push_back(env_item(F, net, s11, S_TD, {y4}, p11.frame(FD), {y3}));
+      gdr.push_back(env_item(F, net, s11, S_CDR, {y5}, {}, {y4}));
+      gdr.push_back(env_item(F, net, s11, S_TR, {cr}, p11.frame(FR), {y5}));
+      push_site(gdr, net, p11);
+      Labels rcut = net.res(cat({p01.frame(FD), {cr}}));
+      Labels lcutN = net.res(cat({{cu}, p00.frame(FD)}));
+      Labels lcutS = net.res(cat({{cl}, p10.frame(FU)}));
+      Labels outN = cat({rcut, lcutN}), outS = cat({rcut, lcutS});
+      Item Gul = contract_greedy(E, net, gul), Gur = contract_greedy(E, net, gur);
+      Item Nn = contract_greedy(E, net, {Gul, Gur}, &outN);
+      Item Gdl = contract_greedy(E, net, gdl), Gdr = contract_greedy(E, net, gdr);
+      Item Ss = contract_greedy(E, net, {Gdl, Gdr}, &outS);
+      PairIn& pi = pin[i];
+      pi.N = Nn.t;
+      pi.S = Ss.t;
+      pi.n_r = numel_of(rcut, net);
+      pi.n_l = numel_of(lcutN, net);
+      CTM_CHECK(pi.n_l == numel_of(lcutS, net), CTM_ERR_INVALID_ARG, "left cut sizes differ");
+      pi.pdims.clear();
+      for (int x : lcutN) pi.pdims.push_back(net.dim[x]);
+      pi.pdims.push_back(chi);
+      pi.qdims.clear();
+      for (int x : lcutS) pi.qdims.push_back(net.dim[x]);
+      pi.qdims.push_back(chi);
+    }
+    std::vector<Tensor> P, Q;
+    projectors(h, pin, P, Q);
+    // absorb column j into the left environment of column j + 1
+    std::vector<std::array<Tensor, 3>> nw(F.FR);
+    for (int i = 0; i < F.FR; ++i) {
+      const int im = mod(i - 1, F.FR);
+      const int s = F.site(i, j);
+      Net net;
+      Pos p = make_pos(h, net, s, q, false);
+      const Labels U = p.frame(FU), D = p.frame(FD), L = p.frame(FL), Rr = p.frame(FR);
+      {  // C_ul' = C_ul T_u P_{i-1}  -> ring [down, right]
+        int pc = net.make(chi), r1 = net.make(chi), rr = net.make(chi), kn = net.make(chi);
+        std::vector<Item> v;
+        v.push_back(env_item(F, net, s, S_CUL, {pc}, {}, {r1}));
+        v.push_back(env_item(F, net, s, S_TU, {r1}, U, {rr}));
+        v.push_back({P[im], net.res(cat({{pc}, U, {kn}}))});
+        Labels o = net.res({kn, rr});
+        nw[i][0] = E.normalize(contract_greedy(E, net, v, &o).t);
+      }
+      {  // T_l' = Q_{i-1} T_l a P_i  -> ring [down, in, up]
+        int c1 = net.make(chi), c2 = net.make(chi), up = net.make(chi), dn = net.make(chi);
+        std::vector<Item> v;
+        v.push_back(env_item(F, net, s, S_TL, {c1}, L, {c2}));
+        push_site(v, net, p);
+        v.push_back({Q[im], net.res(cat({{c2}, U, {up}}))});
+        v.push_back({P[i], net.res(cat({{c1}, D, {dn}}))});
+        Labels o = net.res(cat({{dn}, Rr, {up}}));
+        nw[i][1] = E.normalize(contract_greedy(E, net, v, &o).t);
+      }
+      {  // C_dl' = C_dl T_d Q_i -> ring [right, up]
+        int c3 = net.make(chi), c4 = net.make(chi), c5 = net.make(chi), un = net.make(chi);
+        std::vector<Item> v;
+        v.push_back(env_item(F, net, s, S_CDL, {c3}, {}, {c4}));
+        v.push_back(env_item(F, net, s, S_TD, {c5}, D, {c3}));
+        v.push_back({Q[i], net.res(cat({{c4}, D, {un}}))});
+        Labels o = net.res({c5, un});
+        nw[i][2] = E.normalize(contract_greedy(E, net, v, &o).t);
+      }
+    }
+    for (int i = 0; i < F.FR; ++i) {
+      const int t = F.site(i, j + 1);
+      const int ks[3] = {F.slot(S_CUL), F.slot(S_TL), F.slot(S_CDL)};
+      for (int k = 0; k < 3; ++k) {
+        Tensor v = nw[i][k];
+        Tensor& slot = h->slots[t][ks[k]];
+        CTM_CHECK(v.numel() == slot.numel(), CTM_ERR_INVALID_ARG, "environment shape changed");
+        if (E.recording()) {
+          v.dims = slot.dims;
+          h->env[t][ks[k]] = v;
+        } else {
+          CTM_CUDA(cudaMemcpyAsync(slot.p, v.p, v.bytes(), cudaMemcpyDeviceToDevice, h->st));
+          h->env[t][ks[k]] = slot;
+        }
+      }
+    }
+    if (!E.recording()) h->tape->release(mark);
+  }
+}
+
+void one_iteration(ctm_handle* h) {
+  h->cur_pair = 0;
+  for (int q : {0, 2, 1, 3}) left_move(h, q);  // left, right, up, down
+}
+
+// ------------------------------------------------------------------ energy
+// Blocks (rows x cols of nested sites at (2y, 2x)) and the positions of the two open Y's.
+struct BlockSpec {
+  int h, w, a1, b1, a2, b2;
+};
+BlockSpec block_of(int kind) {
+  switch (kind) {
+    case CTM_BOND_H: return {2, 4, 0, 1, 0, 3};
+    case CTM_BOND_V: return {4, 2, 0, 1, 2, 1};
+    case CTM_BOND_DIAG_DR: return {4, 4, 0, 1, 2, 3};
+    default: return {4, 4, 0, 3, 2, 1};
+  }
+}
+
+Tensor bond_rdm(ctm_handle* h, const ctm_handle::TermH& t) {
+  Engine& E = *h->eng;
+  Frame F(h, 0);
+  BlockSpec bs = block_of(t.kind);
+  const int64_t chi = h->d.chi;
+  const int i0 = 2 * t.y, j0 = 2 * t.x;
+  Net net;
+  std::vector<Pos> pos(bs.h * bs.w);
+  for (int a = 0; a < bs.h; ++a)
+    for (int b = 0; b < bs.w; ++b) {
+      bool imp = (a == bs.a1 && b == bs.b1) || (a == bs.a2 && b == bs.b2);
+      pos[a * bs.w + b] = make_pos(h, net, F.site(i0 + a, j0 + b), 0, imp);
+    }
+  for (int a = 0; a < bs.h; ++a)
+    for (int b = 0; b < bs.w; ++b) {
+      if (b + 1 < bs.w) bond(net, pos[a * bs.w + b], FR, pos[a * bs.w + b + 1], FL);
+      if (a + 1 < bs.h) bond(net, pos[a * bs.w + b], FD, pos[(a + 1) * bs.w + b], FU);
+    }
+  std::vector<int> TU(bs.w + 1), TD(bs.w + 1), TL(bs.h + 1), TR(bs.h + 1);
+  for (auto* v : {&TU, &TD})
+    for (auto& x : *v) x = net.make(chi);
+  for (auto* v : {&TL, &TR})
+    for (auto& x : *v) x = net.make(chi);
+  std::map<int, std::vector<Item>> groups;
+  auto G = [&](int a, int b) { return (a / 2) * 16 + (b / 2); };
+  auto P = [&](int a, int b) -> Pos& { return pos[a * bs.w + b]; };
+  for (int a = 0; a < bs.h; ++a)
+    for (int b = 0; b < bs.w; ++b) push_site(groups[G(a, b)], net, P(a, b));
+  const int H = bs.h - 1, W = bs.w - 1;
+  groups[G(0, 0)].push_back(env_item(F, net, P(0, 0).site, S_CUL, {TL[0]}, {}, {TU[0]}));
+  groups[G(0, W)].push_back(env_item(F, net, P(0, W).site, S_CUR, {TU[bs.w]}, {}, {TR[0]}));
+  groups[G(H, W)].push_back(env_item(F, net, P(H, W).site, S_CDR, {TR[bs.h]}, {}, {TD[bs.w]}));
+  groups[G(H, 0)].push_back(env_item(F, net, P(H, 0).site, S_CDL, {TD[0]}, {}, {TL[bs.h]}));
+  for (int b = 0; b < bs.w; ++b) {
+    groups[G(0, b)].push_back(env_item(F, net, P(0, b).site, S_TU, {TU[b]}, P(0, b).frame(FU), {TU[b + 1]}));
+    groups[G(H, b)].push_back(env_item(F, net, P(H, b).site, S_TD, {TD[b + 1]}, P(H, b).frame(FD), {TD[b]}));
+  }
+  for (int a = 0; a < bs.h; ++a) {
+    groups[G(a, 0)].push_back(env_item(F, net, P(a, 0).site, S_TL, {TL[a + 1]}, P(a, 0).frame(FL), {TL[a]}));
+    groups[G(a, W)].push_back(env_item(F, net, P(a, W).site, S_TR, {TR[a]}, P(a, W).frame(FR), {TR[a + 1]}));
+  }
+  std::vector<Item> parts;
+  for (auto& g : groups) parts.push_back(contract_greedy(E, net, g.second));
+  const Pos& i1 = P(bs.a1, bs.b1);
+  const Pos& i2 = P(bs.a2, bs.b2);
+  Labels out = net.res({i1.s_ket, i2.s_ket, i1.s_bra, i2.s_bra});
+  return contract_greedy(E, net, parts, &out).t;
+}
+
+// energy of the current environment; optionally seeds dE = 1 into the RDM gradients.
+void energy_op(ctm_handle* h, double* e_site, double* e_bonds, bool backward_seed) {
+  Engine& E = *h->eng;
+  const int nt = (int)h->terms.size();
+  const int d2 = h->d.d * h->d.d;
+  std::vector<Tensor> rho(nt);
+  double* rho64 = (double*)E.arena().alloc(sizeof(double) * nt * d2 * d2);
+  for (int t = 0; t < nt; ++t) {
+    rho[t] = bond_rdm(h, h->terms[t]);
+    cast(rho[t].p, rho[t].dt, rho64 + (int64_t)t * d2 * d2, F64, (int64_t)d2 * d2, false, h->st);
+  }
+  double* drho = backward_seed ? (double*)E.arena().alloc(sizeof(double) * nt * d2 * d2) : nullptr;
+  energy_terms(rho64, h->hs, h->coup, nt, d2, 1.0 / (h->d.Lx * h->d.Ly), e_bonds, e_site, drho, h->dstatus, h->st);
+  if (backward_seed)
+    for (int t = 0; t < nt; ++t)
+      if (rho[t].id >= 0) E.seed_grad(rho[t], drho + (int64_t)t * d2 * d2, F64);
+}
+
+// ------------------------------------------------------------------ device state
+void ensure_device(ctm_handle* h) {
+  if (h->dev_ready) return;
+  h->persist.reset(new Arena(size_t(64) << 20));
+  h->tape.reset(new Arena(size_t(256) << 20));
+  h->store.reset(new Arena(size_t(256) << 20));
+  h->eng.reset(new Engine(h->st, h->tape.get()));
+  const int64_t chi = h->d.chi, D = h->d.D, d = h->d.d;
+  h->slots.resize(h->nsites);
+  h->env.resize(h->nsites);
+  h->denv.resize(h->nsites);
+  for (int s = 0; s < h->nsites; ++s) {
+    int i = s / h->C, j = s % h->C;
+    auto ld = leg_dims(kind_of(i, j), D, d);
+    for (int k = 0; k < 8; ++k) {
+      std::vector<int64_t> dims;
+      if (k % 2 == 0) {
+        dims = {chi, chi};
+      } else {
+        int leg = ((k - 1) / 2 + 1) % 4;
+        dims = {chi};
+        for (auto x : ld[leg]) dims.push_back(x);
+        dims.push_back(chi);
+      }
+      Tensor t;
+      t.dt = h->edt;
+      t.dims = dims;
+      t.p = h->persist->alloc(t.bytes());
+      h->slots[s][k] = t;
+      h->env[s][k] = t;
+      Tensor g = t;
+      g.p = h->persist->alloc(t.bytes());
+      h->denv[s][k] = g;
+    }
+  }
+  int64_t n = (int64_t)h->d.Lx * h->d.Ly * d * D * D * D * D;
+  h->A64.dt = F64;
+  h->A64.dims = {n};
+  h->A64.p = h->persist->alloc(n * 8);
+  h->Amode = h->A64;
+  if (h->edt != F64) {
+    h->Amode.dt = h->edt;
+    h->Amode.p = h->persist->alloc(n * dtype_size(h->edt));
+  }
+  int64_t en = ctm_env_numel(h);
+  h->env0 = (double*)h->persist->alloc(en * 8);
+  h->dstatus = (int*)h->persist->alloc(64);
+  h->dsweeps = (int*)h->persist->alloc(64);
+  h->dscal = (double*)h->persist->alloc(64);
+  const int nt = (int)h->terms.size(), d2 = (int)(d * d);
+  h->hs = (double*)h->persist->alloc(sizeof(double) * nt * d2 * d2);
+  h->coup = (double*)h->persist->alloc(sizeof(double) * nt);
+  std::vector<double> hh, cc;
+  for (auto& t : h->terms) {
+    hh.insert(hh.end(), t.h.begin(), t.h.end());
+    cc.push_back(t.coup);
+  }
+  CTM_CUDA(cudaMemcpy(h->hs, hh.data(), sizeof(double) * hh.size(), cudaMemcpyHostToDevice));
+  CTM_CUDA(cudaMemcpy(h->coup, cc.data(), sizeof(double) * cc.size(), cudaMemcpyHostToDevice));
+  CTM_CUDA(cudaMemset(h->dstatus, 0, 64));
+  h->dev_ready = true;
+}
+
+// copy a FP64 ring-layout environment into the slots (dtype of the mode)
+void load_env(ctm_handle* h, const double* src) {
+  int64_t off = 0;
+  for (int s = 0; s < h->nsites; ++s)
+    for (int k = 0; k < 8; ++k) {
+      Tensor& t = h->slots[s][k];
+      cast(src + off, F64, t.p, t.dt, t.numel(), false, h->st);
+      h->env[s][k] = t;
+      off += t.numel();
+    }
+}
+
+void save_env(ctm_handle* h, double* dst) {
+  int64_t off = 0;
+  for (int s = 0; s < h->nsites; ++s)
+    for (int k = 0; k < 8; ++k) {
+      Tensor& t = h->env[s][k];
+      cast(t.p, t.dt, dst + off, F64, t.numel(), false, h->st);
+      off += t.numel();
+    }
+}
+
+void checkpoint(ctm_handle* h, int it) {
+  if ((int)h->ckpt.size() <= it) h->ckpt.resize(it + 1);
+  auto& c = h->ckpt[it];
+  if (c.empty()) {
+    c.resize(h->nsites);
+    for (int s = 0; s < h->nsites; ++s)
+      for (int k = 0; k < 8; ++k) {
+        c[s][k] = h->slots[s][k];
+        c[s][k].p = h->store->alloc(h->slots[s][k].bytes());
+      }
+  }
+  for (int s = 0; s < h->nsites; ++s)
+    for (int k = 0; k < 8; ++k)
+      CTM_CUDA(cudaMemcpyAsync(c[s][k].p, h->env[s][k].p, c[s][k].bytes(), cudaMemcpyDeviceToDevice, h->st));
+}
+
+void forward_iters(ctm_handle* h, int n_iter, double* delta_host) {
+  Engine& E = *h->eng;
+  E.stop_tape();
+  h->replay = false;
+  SiteLeaves sl = site_views(h, false);
+  SiteLeaves* saved = g_sites;
+  g_sites = &sl;
+  for (int k = 0; k < n_iter; ++k) {
+    int it = h->iters_done;
+    checkpoint(h, it);
+    if ((int)h->fac.size() <= it) h->fac.resize(it + 1);
+    h->cur_iter = it;
+    one_iteration(h);
+    h->iters_done++;
+  }
+  g_sites = saved;
+  if (delta_host) {
+    *delta_host = -1.0;
+    int it = h->iters_done - 1;
+    if (it >= 1) {
+      CTM_CUDA(cudaMemsetAsync(h->dscal, 0, sizeof(double), h->st));
+      auto& a = h->fac[it];
+      auto& b = h->fac[it - 1];
+      for (size_t p = 0; p < a.size() && p < b.size(); ++p)
+        spectrum_delta(a[p].lam, b[p].lam, 1, a[p].r, std::min(h->d.chi, a[p].r), h->dscal, h->st);
+      CTM_CUDA(cudaMemcpyAsync(delta_host, h->dscal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    }
+  }
+  sync_status(h);
+}
+
+}  // namespace
+}  // namespace ctm
+
+// ==================================================================== C ABI
+namespace {
+int guard(ctm_handle* h, const std::function<void()>& fn) {
+  try {
+    if (h) ctm::g_launch_counter = &h->launches;
+    fn();
+    ctm::g_launch_counter = nullptr;
+    return CTM_OK;
+  } catch (const ctm::Error& e) {
+    ctm::g_launch_counter = nullptr;
+    if (h) h->last_error = e.what();
+    fprintf(stderr, "libctm: %s\n", e.what());
+    return e.status;
+  } catch (const std::exception& e) {
+    ctm::g_launch_counter = nullptr;
+    if (h) h->last_error = e.what();
+    fprintf(stderr, "libctm: %s\n", e.what());
+    return CTM_ERR_INVALID_ARG;
+  }
+}
+}  // namespace
+
+extern "C" {
+
+int ctm_create(const ctm_desc* desc, ctm_handle** out) {
+  if (!desc || !out) return CTM_ERR_INVALID_ARG;
+  const ctm_desc& d = *desc;
+  if (d.Lx < 1 || d.Ly < 1 || d.d < 1 || d.D < 1 || d.chi < 1 || d.n_terms < 1 || d.n_terms > 64 || !d.terms)
+    return CTM_ERR_INVALID_ARG;
+  if (d.precision < CTM_FP64 || d.precision > CTM_BF16X3) return CTM_ERR_INVALID_ARG;
+  for (int t = 0; t < d.n_terms; ++t) {
+    const ctm_term& tt = d.terms[t];
+    if (!tt.h || tt.x < 0 || tt.x >= d.Lx || tt.y < 0 || tt.y >= d.Ly || tt.kind < 0 || tt.kind > 3)
+      return CTM_ERR_INVALID_ARG;
+  }
+  auto* h = new ctm_handle();
+  h->d = d;
+  h->d.terms = nullptr;
+  h->R = 2 * d.Ly;
+  h->C = 2 * d.Lx;
+  h->nsites = h->R * h->C;
+  h->edt = d.precision == CTM_FP64 ? ctm::F64 : ctm::F32;
+  h->cut = d.svd_cutoff_rel > 0 ? d.svd_cutoff_rel : 1e-6;
+  h->eps = d.svd_adjoint_eps >= 0 ? d.svd_adjoint_eps : 1e-30;
+  int d2 = d.d * d.d;
+  for (int t = 0; t < d.n_terms; ++t) {
+    const ctm_term& tt = d.terms[t];
+    h->terms.push_back({tt.x, tt.y, tt.kind, tt.coupling, std::vector<double>(tt.h, tt.h + d2 * d2)});
+  }
+  *out = h;
+  return CTM_OK;
+}
+
+int ctm_init(ctm_handle* h, const double* A, const double* env0, void* stream) {
+  if (!h || !A) return CTM_ERR_INVALID_ARG;
+  return guard(h, [&]() {
+    h->st = (cudaStream_t)stream;
+    ctm::ensure_device(h);
+    h->eng->set_stream(h->st);
+    int64_t n = h->A64.numel();
+    CTM_CUDA(cudaMemcpyAsync(h->A64.p, A, n * 8, cudaMemcpyDeviceToDevice, h->st));
+    if (h->edt != ctm::F64) ctm::cast(h->A64.p, ctm::F64, h->Amode.p, h->edt, n, false, h->st);
+    if (env0) {
+      CTM_CUDA(cudaMemcpyAsync(h->env0, env0, ctm_env_numel(h) * 8, cudaMemcpyDeviceToDevice, h->st));
+    } else {
+      ctm::save_env(h, h->env0);
+    }
+    ctm::load_env(h, h->env0);
+    h->iters_done = 0;
+    h->fac.clear();
+    h->ckpt.clear();
+    h->store->release({0, 0});
+    CTM_CUDA(cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->st));
+    h->inited = true;
+    CTM_CUDA(cudaStreamSynchronize(h->st));
+  });
+}
+
+int ctm_step(ctm_handle* h, int n_iter, double* delta_host, void* stream) {
+  if (!h || n_iter < 0) return CTM_ERR_INVALID_ARG;
+  if (!h->inited) return CTM_ERR_STATE;
+  return guard(h, [&]() {
+    h->st = (cudaStream_t)stream;
+    h->eng->set_stream(h->st);
+    ctm::forward_iters(h, n_iter, delta_host);
+  });
+}
+
+int ctm_energy(ctm_handle* h, double* e_site_dev, double* e_bonds_dev, void* stream) {
+  if (!h || !e_site_dev) return CTM_ERR_INVALID_ARG;
+  if (!h->inited) return CTM_ERR_STATE;
+  return guard(h, [&]() {
+    h->st = (cudaStream_t)stream;
+    h->eng->set_stream(h->st);
+    h->eng->stop_tape();
+    auto mark = h->tape->mark();
+    ctm::SiteLeaves sl = ctm::site_views(h, false);
+    ctm::g_sites = &sl;
+    ctm::energy_op(h, e_site_dev, e_bonds_dev, false);
+    ctm::g_sites = nullptr;
+    h->tape->release(mark);
+    ctm::sync_status(h);
+  });
+}
+
+int ctm_grad(ctm_handle* h, int n_iter, double* e_site_dev, double* dA_dev, void* stream) {
+  if (!h || !e_site_dev || !dA_dev || n_iter < 0) return CTM_ERR_INVALID_ARG;
+  if (!h->inited) return CTM_ERR_STATE;
+  return guard(h, [&]() {
+    using namespace ctm;
+    h->st = (cudaStream_t)stream;
+    Engine& E = *h->eng;
+    E.set_stream(h->st);
+    // forward from the initial environment
+    load_env(h, h->env0);
+    h->iters_done = 0;
+    forward_iters(h, n_iter, nullptr);
+    const int64_t nA = h->A64.numel();
+    CTM_CUDA(cudaMemsetAsync(dA_dev, 0, nA * 8, h->st));
+    // energy with its tape
+    auto mark = h->tape->mark();
+    E.start_tape();
+    SiteLeaves sl = site_views(h, true);
+    g_sites = &sl;
+    for (int s = 0; s < h->nsites; ++s)
+      for (int k = 0; k < 8; ++k) h->env[s][k] = E.leaf(h->env[s][k]);
+    energy_op(h, e_site_dev, nullptr, true);
+    E.backward();
+    auto collect = [&](bool zero_missing) {
+      int64_t per = (int64_t)h->d.d * h->d.D * h->d.D * h->d.D * h->d.D;
+      for (int p = 0; p < (int)sl.t.size(); ++p) {
+        void* g = E.grad(sl.t[p], false);
+        if (g) cast(g, h->edt, dA_dev + per * p, F64, per, true, h->st);
+      }
+      for (int s = 0; s < h->nsites; ++s)
+        for (int k = 0; k < 8; ++k) {
+          void* g = E.grad(h->env[s][k], false);
+          Tensor& dst = h->denv[s][k];
+          if (g)
+            CTM_CUDA(cudaMemcpyAsync(dst.p, g, dst.bytes(), cudaMemcpyDeviceToDevice, h->st));
+          else if (zero_missing)
+            CTM_CUDA(cudaMemsetAsync(dst.p, 0, dst.bytes(), h->st));
+        }
+    };
+    collect(true);
+    h->tape->release(mark);
+    // iterations in reverse, each recomputed from its checkpoint with stored projector factors
+    for (int it = n_iter - 1; it >= 0; --it) {
+      auto m2 = h->tape->mark();
+      E.start_tape();
+      SiteLeaves sl2 = site_views(h, true);
+      g_sites = &sl2;
+      std::vector<std::array<Tensor, 8>> leaves(h->nsites);
+      for (int s = 0; s < h->nsites; ++s)
+        for (int k = 0; k < 8; ++k) leaves[s][k] = h->env[s][k] = E.leaf(h->ckpt[it][s][k]);
+      h->replay = true;
+      h->cur_iter = it;
+      one_iteration(h);
+      h->replay = false;
+      for (int s = 0; s < h->nsites; ++s)
+        for (int k = 0; k < 8; ++k) E.seed_grad(h->env[s][k], h->denv[s][k].p, h->edt);
+      E.backward();
+      int64_t per = (int64_t)h->d.d * h->d.D * h->d.D * h->d.D * h->d.D;
+      for (int p = 0; p < (int)sl2.t.size(); ++p) {
+        void* g = E.grad(sl2.t[p], false);
+        if (g) cast(g, h->edt, dA_dev + per * p, F64, per, true, h->st);
+      }
+      for (int s = 0; s < h->nsites; ++s)
+        for (int k = 0; k < 8; ++k) {
+          void* g = E.grad(leaves[s][k], false);
+          Tensor& dst = h->denv[s][k];
+          if (g)
+            CTM_CUDA(cudaMemcpyAsync(dst.p, g, dst.bytes(), cudaMemcpyDeviceToDevice, h->st));
+          else
+            CTM_CUDA(cudaMemsetAsync(dst.p, 0, dst.bytes(), h->st));
+        }
+      h->tape->release(m2);
+    }
+    g_sites = nullptr;
+    // leave the handle holding the final environment
+    for (int s = 0; s < h->nsites; ++s)
+      for (int k = 0; k < 8; ++k) h->env[s][k] = h->slots[s][k];
+    sync_status(h);
+  });
+}
+
+int ctm_get_env(ctm_handle* h, double* env_dev, void* stream) {
+  if (!h || !env_dev) return CTM_ERR_INVALID_ARG;
+  if (!h->inited) return CTM_ERR_STATE;
+  return guard(h, [&]() {
+    h->st = (cudaStream_t)stream;
+    ctm::save_env(h, env_dev);
+    CTM_CUDA(cudaStreamSynchronize(h->st));
+  });
+}
+
+int ctm_set_env(ctm_handle* h, const double* env_dev, void* stream) {
+  if (!h || !env_dev) return CTM_ERR_INVALID_ARG;
+  return guard(h, [&]() {
+    h->st = (cudaStream_t)stream;
+    ctm::ensure_device(h);
+    ctm::load_env(h, env_dev);
+    CTM_CUDA(cudaStreamSynchronize(h->st));
+  });
+}
+
+int64_t ctm_env_numel(const ctm_handle* h) {
+  if (!h) return -1;
+  const int64_t chi = h->d.chi, D = h->d.D, d = h->d.d;
+  int64_t n = 0;
+  for (int s = 0; s < h->nsites; ++s) {
+    auto ld = ctm::leg_dims(ctm::kind_of(s / h->C, s % h->C), D, d);
+    for (int k = 0; k < 8; ++k) {
+      if (k % 2 == 0) {
+        n += chi * chi;
+      } else {
+        int64_t b = 1;
+        for (auto x : ld[((k - 1) / 2 + 1) % 4]) b *= x;
+        n += chi * b * chi;
+      }
+    }
+  }
+  return n;
+}
+
+int64_t ctm_kernel_launches(const ctm_handle* h) { return h ? h->launches : -1; }
+
+int ctm_destroy(ctm_handle* h) {
+  if (!h) return CTM_ERR_INVALID_ARG;
+  h->eng.reset();
+  h->persist.reset();
+  h->tape.reset();
+  h->store.reset();
+  delete h;
+  return CTM_OK;
+}
+
+const char* ctm_error_string(int s) {
+  switch (s) {
+    case CTM_OK: return "ok";
+    case CTM_ERR_INVALID_ARG: return "invalid argument";
+    case CTM_ERR_CUDA: return "CUDA runtime error";
+    case CTM_ERR_OOM: return "out of device memory";
+    case CTM_ERR_NONFINITE: return "non-finite value";
+    case CTM_ERR_SVD_NOCONV: return "SVD did not converge";
+    case CTM_ERR_DEGENERATE: return "degenerate spectrum";
+    case CTM_ERR_TIMEOUT: return "device wait timed out";
+    case CTM_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

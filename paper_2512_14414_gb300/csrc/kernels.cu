@@ -1,0 +1,598 @@
+// Element-wise, permutation, SIMT GEMM, projector-helper and energy kernels of libctm.
+#include "kernels.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace ctm {
+
+thread_local int64_t* g_launch_counter = nullptr;
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ double to_d(T v) { return (double)v; }
+template <>
+__device__ __forceinline__ double to_d<__nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
+template <typename T>
+__device__ __forceinline__ T from_d(double v) { return (T)v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(double v) { return __float2bfloat16((float)v); }
+
+inline int nblocks(int64_t n, int per_block, int cap = 65535 * 8) {
+  int64_t b = (n + per_block - 1) / per_block;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, cap));
+}
+
+// ------------------------------------------------------------------ permutation
+struct PermDev {
+  int rank;
+  int64_t dims[8];
+  int64_t istr[8];
+  int64_t ostr[8];
+};
+
+template <typename Ti, typename To, bool ACC>
+__global__ void permute_generic(const Ti* __restrict__ in, To* __restrict__ out, PermDev p, int64_t n, double scale) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = idx, src = 0;
+#pragma unroll 8
+    for (int k = 7; k >= 0; --k) {
+      if (k < p.rank) {
+        int64_t c = rem % p.dims[k];
+        rem /= p.dims[k];
+        src += c * p.istr[k];
+      }
+    }
+    double v = scale * to_d(in[src]);
+    if (ACC) v += to_d(out[idx]);
+    out[idx] = from_d<To>(v);
+  }
+}
+
+// Tiled transpose: output innermost dim `a` (in-stride sa) and the output dim `b` with input stride 1.
+struct PermTile {
+  int64_t Na, Nb, sa, ob;  // sizes, in-stride of a, out-stride of b
+  int nrest;
+  int64_t rdims[8], ristr[8], rostr[8];
+  int64_t nrest_total;
+};
+
+template <typename Ti, typename To, bool ACC>
+__global__ void permute_tiled(const Ti* __restrict__ in, To* __restrict__ out, PermTile p, double scale) {
+  __shared__ double tile[32][33];
+  const int64_t tiles_a = (p.Na + 31) / 32;
+  const int64_t ta = blockIdx.x % tiles_a, tb = blockIdx.x / tiles_a;
+  const int64_t a0 = ta * 32, b0 = tb * 32;
+  for (int64_t rest = blockIdx.y; rest < p.nrest_total; rest += gridDim.y) {
+    int64_t rem = rest, ioff = 0, ooff = 0;
+    for (int k = p.nrest - 1; k >= 0; --k) {
+      int64_t c = rem % p.rdims[k];
+      rem /= p.rdims[k];
+      ioff += c * p.ristr[k];
+      ooff += c * p.rostr[k];
+    }
+    __syncthreads();
+    for (int ty = threadIdx.y; ty < 32; ty += blockDim.y) {
+      int64_t ai = a0 + ty, bi = b0 + threadIdx.x;
+      if (ai < p.Na && bi < p.Nb) tile[ty][threadIdx.x] = to_d(in[ioff + ai * p.sa + bi]);
+    }
+    __syncthreads();
+    for (int ty = threadIdx.y; ty < 32; ty += blockDim.y) {
+      int64_t bi = b0 + ty, ai = a0 + threadIdx.x;
+      if (ai < p.Na && bi < p.Nb) {
+        int64_t o = ooff + bi * p.ob + ai;
+        double v = scale * tile[threadIdx.x][ty];
+        if (ACC) v += to_d(out[o]);
+        out[o] = from_d<To>(v);
+      }
+    }
+  }
+}
+
+template <typename Ti, typename To>
+void permute_t(const Ti* in, To* out, const PermSpec& ps, bool acc, double scale, cudaStream_t st) {
+  int r = ps.rank;
+  int64_t n = 1;
+  for (int k = 0; k < r; ++k) n *= ps.out_dims[k];
+  if (n == 0) return;
+  int64_t ostr[8];
+  int64_t s = 1;
+  for (int k = r - 1; k >= 0; --k) {
+    ostr[k] = s;
+    s *= ps.out_dims[k];
+  }
+  int b = -1;
+  for (int k = 0; k < r - 1; ++k)
+    if (ps.in_stride[k] == 1 && ps.out_dims[k] > 1) b = k;
+  bool tiled = r >= 2 && ps.in_stride[r - 1] != 1 && b >= 0 && ps.out_dims[r - 1] >= 8 && ps.out_dims[b] >= 8;
+  if (tiled) {
+    PermTile p{};
+    p.Na = ps.out_dims[r - 1];
+    p.sa = ps.in_stride[r - 1];
+    p.Nb = ps.out_dims[b];
+    p.ob = ostr[b];
+    p.nrest = 0;
+    p.nrest_total = 1;
+    for (int k = 0; k < r - 1; ++k) {
+      if (k == b) continue;
+      p.rdims[p.nrest] = ps.out_dims[k];
+      p.ristr[p.nrest] = ps.in_stride[k];
+      p.rostr[p.nrest] = ostr[k];
+      p.nrest_total *= ps.out_dims[k];
+      p.nrest++;
+    }
+    dim3 grid((unsigned)(((p.Na + 31) / 32) * ((p.Nb + 31) / 32)), (unsigned)std::min<int64_t>(p.nrest_total, 65535));
+    dim3 block(32, 8);
+    if (acc)
+      permute_tiled<Ti, To, true><<<grid, block, 0, st>>>(in, out, p, scale);
+    else
+      permute_tiled<Ti, To, false><<<grid, block, 0, st>>>(in, out, p, scale);
+  } else {
+    PermDev p{};
+    p.rank = r;
+    for (int k = 0; k < r; ++k) {
+      p.dims[k] = ps.out_dims[k];
+      p.istr[k] = ps.in_stride[k];
+    }
+    int bl = nblocks(n, 256);
+    if (acc)
+      permute_generic<Ti, To, true><<<bl, 256, 0, st>>>(in, out, p, n, scale);
+    else
+      permute_generic<Ti, To, false><<<bl, 256, 0, st>>>(in, out, p, n, scale);
+  }
+  CTM_LAUNCHED();
+}
+
+// ------------------------------------------------------------------ SIMT GEMM
+template <typename T, int BM, int BN, int BK>
+__global__ void __launch_bounds__(256) gemm_simt(const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ C,
+                                                 GemmSpec g) {
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+  for (int64_t bb = blockIdx.z; bb < g.batch; bb += gridDim.z) {
+    const T* Ab = A + bb * g.strideA;
+    const T* Bb = B + bb * g.strideB;
+    T* Cb = C + bb * g.strideC;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int64_t k0 = 0; k0 < g.K; k0 += BK) {
+#pragma unroll
+      for (int q = 0; q < (BM * BK) / 256; ++q) {
+        int e = threadIdx.x + 256 * q;
+        int ml, kl;
+        if (g.transA) {
+          ml = e % BM;
+          kl = e / BM;
+        } else {
+          kl = e % BK;
+          ml = e / BK;
+        }
+        int64_t m = m0 + ml, k = k0 + kl;
+        T v = T(0);
+        if (m < g.M && k < g.K) v = g.transA ? Ab[k * g.lda + m] : Ab[m * g.lda + k];
+        As[kl][ml] = v;
+      }
+#pragma unroll
+      for (int q = 0; q < (BN * BK) / 256; ++q) {
+        int e = threadIdx.x + 256 * q;
+        int nl, kl;
+        if (g.transB) {
+          kl = e % BK;
+          nl = e / BK;
+        } else {
+          nl = e % BN;
+          kl = e / BN;
+        }
+        int64_t n = n0 + nl, k = k0 + kl;
+        T v = T(0);
+        if (n < g.N && k < g.K) v = g.transB ? Bb[n * g.ldb + k] : Bb[k * g.ldb + n];
+        Bs[kl][nl] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        T a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int64_t m = m0 + ty + 16 * i;
+      if (m >= g.M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int64_t n = n0 + tx + 16 * j;
+        if (n >= g.N) continue;
+        T v = (T)g.alpha * acc[i][j];
+        if (g.beta != 0.0) v += (T)g.beta * Cb[m * g.ldc + n];
+        Cb[m * g.ldc + n] = v;
+      }
+    }
+  }
+}
+
+template <typename T>
+void gemm_t(const T* A, const T* B, T* C, const GemmSpec& g, cudaStream_t st) {
+  if (g.M == 0 || g.N == 0 || g.batch == 0) return;
+  if (g.K == 0) {  // C = beta C
+    CTM_CHECK(g.beta == 0.0, CTM_ERR_INVALID_ARG, "gemm with K=0 and beta!=0 unsupported");
+    for (int64_t b = 0; b < g.batch; ++b)
+      for (int64_t m = 0; m < g.M; ++m) CTM_CUDA(cudaMemsetAsync(C + b * g.strideC + m * g.ldc, 0, g.N * sizeof(T), st));
+    return;
+  }
+  dim3 grid((unsigned)((g.N + 63) / 64), (unsigned)((g.M + 63) / 64), (unsigned)std::min<int64_t>(g.batch, 65535));
+  CTM_CHECK((g.M + 63) / 64 < 65536, CTM_ERR_INVALID_ARG, "gemm M too large");
+  gemm_simt<T, 64, 64, 16><<<grid, 256, 0, st>>>(A, B, C, g);
+  CTM_LAUNCHED();
+}
+
+// ------------------------------------------------------------------ element-wise
+template <typename T>
+__global__ void fill_k(T* p, int64_t n, double v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = from_d<T>(v);
+}
+
+template <typename Ti, typename To, bool ACC>
+__global__ void cast_k(const Ti* in, To* out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = to_d(in[i]);
+    if (ACC) v += to_d(out[i]);
+    out[i] = from_d<To>(v);
+  }
+}
+
+template <typename T>
+__global__ void sumsq_partial(const T* x, int64_t n, double* part) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = to_d(x[i]);
+    s = fma(v, v, s);
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void sum_final(const double* part, int n, double* out) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+template <typename T>
+__global__ void scale_rsqrt_k(const T* x, int64_t n, const double* ss, T* y, double* inv) {
+  double s = *ss;
+  double f = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && inv) *inv = f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = from_d<T>(to_d(x[i]) * f);
+}
+
+template <typename T, bool ACC>
+__global__ void scale_by_k(const T* dy, int64_t n, const double* inv, T* dx) {
+  double f = *inv;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = to_d(dy[i]) * f;
+    if (ACC) v += to_d(dx[i]);
+    dx[i] = from_d<T>(v);
+  }
+}
+
+// ------------------------------------------------------------------ projector helpers
+__global__ void proj_prepare_k(const double* lam, double* U, double* V, double* inv, double* sinv, int64_t n_r, int r,
+                               int kept, double cut, double rank_tol, int* status) {
+  const int b = blockIdx.y;
+  const double* l = lam + (int64_t)b * r;
+  const double l0 = l[0];
+  if (blockIdx.x == 0) {
+    for (int k = threadIdx.x; k < r; k += blockDim.x) {
+      double v = l[k];
+      if (!isfinite(v)) atomicOr(status, DEV_NONFINITE);
+      sinv[(int64_t)b * r + k] = (v > rank_tol * l0) ? 1.0 / v : 0.0;
+      if (k < kept) inv[(int64_t)b * kept + k] = (v > cut * l0) ? 1.0 / sqrt(v) : 0.0;
+    }
+    if (threadIdx.x == 0 && !(l0 > 0.0)) atomicOr(status, DEV_DEGENERATE);
+  }
+  int64_t total = n_r * r;
+  double* Ub = U + (int64_t)b * total;
+  double* Vb = V + (int64_t)b * total;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int k = (int)(e % r);
+    if (!(l[k] > rank_tol * l0)) {
+      Ub[e] = 0.0;
+      Vb[e] = 0.0;
+    }
+  }
+}
+
+__global__ void scale_cols_k(const double* Y, int64_t ldy, int64_t strideY, const double* s, int64_t strideS, double* X,
+                             int64_t n, int kept) {
+  const int b = blockIdx.y;
+  int64_t total = n * kept;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / kept;
+    int k = (int)(e % kept);
+    X[(int64_t)b * total + e] = Y[(int64_t)b * strideY + i * ldy + k] * s[(int64_t)b * strideS + k];
+  }
+}
+
+__global__ void proj_dlam_k(const double* dZ, const double* U, const double* dW, const double* V, const double* inv,
+                            double* dl, int64_t n_r, int r, int kept) {
+  const int b = blockIdx.y;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int k = blockIdx.x * (blockDim.x / 32) + warp;
+  if (k >= kept) return;
+  const double* dZb = dZ + (int64_t)b * n_r * kept;
+  const double* dWb = dW + (int64_t)b * n_r * kept;
+  const double* Ub = U + (int64_t)b * n_r * r;
+  const double* Vb = V + (int64_t)b * n_r * r;
+  double s = 0.0;
+  for (int64_t i = lane; i < n_r; i += 32) {
+    s = fma(dZb[i * kept + k], Ub[i * r + k], s);
+    s = fma(dWb[i * kept + k], Vb[i * r + k], s);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    double iv = inv[(int64_t)b * kept + k];
+    dl[(int64_t)b * kept + k] = -0.5 * iv * iv * iv * s;
+  }
+}
+
+__global__ void proj_core_k(const double* Aa, const double* Bb, const double* lam, const double* dl, double* core, int r,
+                            int kept, double rank_tol, double eps) {
+  const int b = blockIdx.y;
+  const double* l = lam + (int64_t)b * r;
+  const double l0 = l[0];
+  const double* A = Aa + (int64_t)b * r * kept;
+  const double* B = Bb + (int64_t)b * r * kept;
+  const double e4 = eps * l0 * l0 * l0 * l0;
+  int64_t total = (int64_t)r * r;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / r), j = (int)(e % r);
+    double li = l[i], lj = l[j];
+    double v = 0.0;
+    if (i == j) {
+      if (i < kept) v = dl[(int64_t)b * kept + i];
+    } else if (li > rank_tol * l0 && lj > rank_tol * l0) {
+      double diff = lj * lj - li * li;
+      double F = diff / (diff * diff + e4);
+      double aij = (j < kept) ? A[(int64_t)i * kept + j] : 0.0;
+      double aji = (i < kept) ? A[(int64_t)j * kept + i] : 0.0;
+      double bij = (j < kept) ? B[(int64_t)i * kept + j] : 0.0;
+      double bji = (i < kept) ? B[(int64_t)j * kept + i] : 0.0;
+      v = F * (aij - aji) * lj + li * F * (bij - bji);
+    }
+    core[(int64_t)b * total + e] = v;
+  }
+}
+
+__global__ void proj_resid_k(const double* dU, const double* X, const double* sinv, double* E, int64_t n_r, int r,
+                             int kept) {
+  const int b = blockIdx.y;
+  int64_t total = n_r * kept;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int k = (int)(e % kept);
+    int64_t o = (int64_t)b * total + e;
+    E[o] = (dU[o] - X[o]) * sinv[(int64_t)b * r + k];
+  }
+}
+
+// ------------------------------------------------------------------ energy
+__global__ void energy_k(const double* rho, const double* hs, const double* coup, int n_terms, int d2, double inv_sites,
+                         double* e_bond, double* e_site, double* drho, int* status) {
+  __shared__ double es[64];
+  __shared__ double trs[64];
+  const int t = threadIdx.x;
+  if (t < n_terms) {
+    const double* R = rho + (int64_t)t * d2 * d2;
+    const double* H = hs + (int64_t)t * d2 * d2;
+    double tr = 0.0, num = 0.0;
+    for (int a = 0; a < d2; ++a) {
+      tr += R[a * d2 + a];
+      for (int c = 0; c < d2; ++c) num = fma(R[a * d2 + c], H[c * d2 + a], num);
+    }
+    double e = num / tr;
+    if (!isfinite(e)) atomicOr(status, DEV_NONFINITE);
+    es[t] = e;
+    trs[t] = tr;
+    if (e_bond) e_bond[t] = e;
+  }
+  __syncthreads();
+  if (t == 0) {
+    double E = 0.0;
+    for (int k = 0; k < n_terms; ++k) E += coup[k] * es[k];
+    *e_site = E * inv_sites;
+  }
+  if (drho && t < n_terms) {
+    const double* H = hs + (int64_t)t * d2 * d2;
+    double f = coup[t] * inv_sites / trs[t];
+    for (int a = 0; a < d2; ++a)
+      for (int c = 0; c < d2; ++c) drho[(int64_t)t * d2 * d2 + a * d2 + c] = f * (H[c * d2 + a] - (a == c ? es[t] : 0.0));
+  }
+}
+
+__global__ void embed_t_k(const double* U, int r, double* X, int64_t m) {
+  int64_t total = (int64_t)r * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t k = e / m, i = e % m;
+    X[e] = (i < r) ? U[i * r + k] : 0.0;
+  }
+}
+
+__global__ void spectrum_delta_k(const double* lam, const double* prev, int batch, int r, int kept, double* out) {
+  __shared__ double sh[256];
+  double best = 0.0;
+  for (int b = 0; b < batch; ++b) {
+    const double* l = lam + (int64_t)b * r;
+    const double* p = prev + (int64_t)b * r;
+    double sl = 0.0, sp = 0.0;
+    for (int k = 0; k < kept; ++k) {
+      sl += l[k];
+      sp += p[k];
+    }
+    for (int k = threadIdx.x; k < kept; k += blockDim.x) {
+      double v = fabs(l[k] / sl - p[k] / sp);
+      best = v > best ? v : best;
+    }
+  }
+  sh[threadIdx.x] = best;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = fmax(*out, sh[0]);
+}
+
+}  // namespace
+
+// ================================================================== host wrappers
+#define DISPATCH_IO(tin, tout, F)                                                                           \
+  if (tin == F64 && tout == F64) { F(double, double); }                                                     \
+  else if (tin == F64 && tout == F32) { F(double, float); }                                                 \
+  else if (tin == F32 && tout == F64) { F(float, double); }                                                 \
+  else if (tin == F32 && tout == F32) { F(float, float); }                                                  \
+  else if (tin == F32 && tout == BF16) { F(float, __nv_bfloat16); }                                         \
+  else if (tin == F64 && tout == BF16) { F(double, __nv_bfloat16); }                                        \
+  else if (tin == BF16 && tout == F32) { F(__nv_bfloat16, float); }                                         \
+  else throw Error(CTM_ERR_INVALID_ARG, "unsupported dtype pair");
+
+void permute(const void* in, DType tin, void* out, DType tout, const PermSpec& p, bool acc, double scale,
+             cudaStream_t st) {
+#define F(Ti, To) permute_t<Ti, To>((const Ti*)in, (To*)out, p, acc, scale, st)
+  DISPATCH_IO(tin, tout, F)
+#undef F
+}
+
+void gemm_f64(const double* A, const double* B, double* C, const GemmSpec& g, cudaStream_t st) { gemm_t(A, B, C, g, st); }
+void gemm_f32(const float* A, const float* B, float* C, const GemmSpec& g, cudaStream_t st) { gemm_t(A, B, C, g, st); }
+
+void fill(void* p, DType t, int64_t n, double v, cudaStream_t st) {
+  if (n == 0) return;
+  int bl = nblocks(n, 256);
+  if (t == F64) fill_k<double><<<bl, 256, 0, st>>>((double*)p, n, v);
+  else if (t == F32) fill_k<float><<<bl, 256, 0, st>>>((float*)p, n, v);
+  else fill_k<__nv_bfloat16><<<bl, 256, 0, st>>>((__nv_bfloat16*)p, n, v);
+  CTM_LAUNCHED();
+}
+
+void cast(const void* in, DType tin, void* out, DType tout, int64_t n, bool acc, cudaStream_t st) {
+  if (n == 0) return;
+  int bl = nblocks(n, 256);
+#define F(Ti, To)                                                                \
+  if (acc) cast_k<Ti, To, true><<<bl, 256, 0, st>>>((const Ti*)in, (To*)out, n); \
+  else cast_k<Ti, To, false><<<bl, 256, 0, st>>>((const Ti*)in, (To*)out, n);
+  DISPATCH_IO(tin, tout, F)
+#undef F
+  CTM_LAUNCHED();
+}
+
+void sumsq(const void* x, DType t, int64_t n, double* out, double* work, cudaStream_t st) {
+  int bl = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (n + 1023) / 1024));
+  if (t == F64) sumsq_partial<double><<<bl, 256, 0, st>>>((const double*)x, n, work);
+  else sumsq_partial<float><<<bl, 256, 0, st>>>((const float*)x, n, work);
+  CTM_LAUNCHED();
+  sum_final<<<1, 256, 0, st>>>(work, bl, out);
+  CTM_LAUNCHED();
+}
+
+void scale_rsqrt(const void* x, DType t, int64_t n, const double* ss, void* y, double* inv, cudaStream_t st) {
+  int bl = nblocks(n, 256);
+  if (t == F64) scale_rsqrt_k<double><<<bl, 256, 0, st>>>((const double*)x, n, ss, (double*)y, inv);
+  else scale_rsqrt_k<float><<<bl, 256, 0, st>>>((const float*)x, n, ss, (float*)y, inv);
+  CTM_LAUNCHED();
+}
+
+void scale_by(const void* dy, DType t, int64_t n, const double* inv, void* dx, bool acc, cudaStream_t st) {
+  int bl = nblocks(n, 256);
+  if (t == F64) {
+    if (acc) scale_by_k<double, true><<<bl, 256, 0, st>>>((const double*)dy, n, inv, (double*)dx);
+    else scale_by_k<double, false><<<bl, 256, 0, st>>>((const double*)dy, n, inv, (double*)dx);
+  } else {
+    if (acc) scale_by_k<float, true><<<bl, 256, 0, st>>>((const float*)dy, n, inv, (float*)dx);
+    else scale_by_k<float, false><<<bl, 256, 0, st>>>((const float*)dy, n, inv, (float*)dx);
+  }
+  CTM_LAUNCHED();
+}
+
+void proj_prepare(const double* lam, double* U, double* V, double* inv, double* sinv, int batch, int64_t n_r, int r,
+                  int kept, double cut, double rank_tol, int* status, cudaStream_t st) {
+  dim3 grid(nblocks(n_r * r, 256, 4096), batch);
+  proj_prepare_k<<<grid, 256, 0, st>>>(lam, U, V, inv, sinv, n_r, r, kept, cut, rank_tol, status);
+  CTM_LAUNCHED();
+}
+
+void scale_cols(const double* Y, int64_t ldy, int64_t strideY, const double* s, int64_t strideS, double* X, int batch,
+                int64_t n, int kept, cudaStream_t st) {
+  dim3 grid(nblocks(n * kept, 256, 4096), batch);
+  scale_cols_k<<<grid, 256, 0, st>>>(Y, ldy, strideY, s, strideS, X, n, kept);
+  CTM_LAUNCHED();
+}
+
+void proj_dlam(const double* dZ, const double* U, const double* dW, const double* V, const double* inv, double* dl,
+               int batch, int64_t n_r, int r, int kept, cudaStream_t st) {
+  dim3 grid((kept + 7) / 8, batch);
+  proj_dlam_k<<<grid, 256, 0, st>>>(dZ, U, dW, V, inv, dl, n_r, r, kept);
+  CTM_LAUNCHED();
+}
+
+void proj_core(const double* Aa, const double* Bb, const double* lam, const double* dl, double* core, int batch, int r,
+               int kept, double rank_tol, double eps, cudaStream_t st) {
+  dim3 grid(nblocks((int64_t)r * r, 256, 4096), batch);
+  proj_core_k<<<grid, 256, 0, st>>>(Aa, Bb, lam, dl, core, r, kept, rank_tol, eps);
+  CTM_LAUNCHED();
+}
+
+void proj_resid(const double* dU, const double* X, const double* sinv, double* E, int batch, int64_t n_r, int r,
+                int kept, cudaStream_t st) {
+  dim3 grid(nblocks(n_r * kept, 256, 4096), batch);
+  proj_resid_k<<<grid, 256, 0, st>>>(dU, X, sinv, E, n_r, r, kept);
+  CTM_LAUNCHED();
+}
+
+void energy_terms(const double* rho, const double* hs, const double* coup, int n_terms, int d2, double inv_sites,
+                  double* e_bond, double* e_site, double* drho, int* status, cudaStream_t st) {
+  CTM_CHECK(n_terms <= 64, CTM_ERR_INVALID_ARG, "at most 64 terms");
+  energy_k<<<1, 64, 0, st>>>(rho, hs, coup, n_terms, d2, inv_sites, e_bond, e_site, drho, status);
+  CTM_LAUNCHED();
+}
+
+void embed_transpose(const double* U, int r, double* X, int64_t m, cudaStream_t st) {
+  embed_t_k<<<nblocks((int64_t)r * m, 256, 4096), 256, 0, st>>>(U, r, X, m);
+  CTM_LAUNCHED();
+}
+
+void spectrum_delta(const double* lam, const double* lam_prev, int batch, int r, int kept, double* out, cudaStream_t st) {
+  spectrum_delta_k<<<1, 256, 0, st>>>(lam, lam_prev, batch, r, kept, out);
+  CTM_LAUNCHED();
+}
+
+}  // namespace ctm

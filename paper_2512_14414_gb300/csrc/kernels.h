@@ -1,0 +1,92 @@
+// Launch wrappers of the CUDA kernels of libctm (all enqueue on `st`, no host sync).
+#pragma once
+#include "common.h"
+
+namespace ctm {
+
+// ------------------------------------------------------------------ permutation
+// out[i_0..i_{r-1}] (row-major over out_dims) = scale * in[sum_k i_k * in_stride[k]]
+// (+= when acc).  in/out dtypes may differ (conversion fused into the copy).
+struct PermSpec {
+  int rank = 0;
+  int64_t out_dims[8] = {0};
+  int64_t in_stride[8] = {0};  // input stride (elements) of each output dimension
+};
+void permute(const void* in, DType tin, void* out, DType tout, const PermSpec& p, bool acc,
+             double scale, cudaStream_t st);
+
+// ------------------------------------------------------------------ GEMM (SIMT)
+// C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b], row-major.
+// op(A) is M x K: A[m*lda+k] (transA=0) or A[k*lda+m] (transA=1);
+// op(B) is K x N: B[k*ldb+n] (transB=0) or B[n*ldb+k] (transB=1).
+struct GemmSpec {
+  int64_t M = 0, N = 0, K = 0, batch = 1;
+  bool transA = false, transB = false;
+  int64_t lda = 0, ldb = 0, ldc = 0;
+  int64_t strideA = 0, strideB = 0, strideC = 0;
+  double alpha = 1.0, beta = 0.0;
+};
+void gemm_f64(const double* A, const double* B, double* C, const GemmSpec& g, cudaStream_t st);
+void gemm_f32(const float* A, const float* B, float* C, const GemmSpec& g, cudaStream_t st);
+
+// ------------------------------------------------------------------ elementwise / reductions
+void fill(void* p, DType t, int64_t n, double v, cudaStream_t st);
+void cast(const void* in, DType tin, void* out, DType tout, int64_t n, bool acc, cudaStream_t st);
+// partial[...] then out = sum of squares of x (deterministic two-pass); work >= 1024 doubles.
+void sumsq(const void* x, DType t, int64_t n, double* out, double* work, cudaStream_t st);
+// y = x * rsqrt(*ss) and *inv = rsqrt(*ss)
+void scale_rsqrt(const void* x, DType t, int64_t n, const double* ss, void* y, double* inv, cudaStream_t st);
+// dx (+)= dy * (*inv)
+void scale_by(const void* dy, DType t, int64_t n, const double* inv, void* dx, bool acc, cudaStream_t st);
+
+// ------------------------------------------------------------------ projector helpers (FP64)
+// Singular values lam (batch x r, descending).  For k < kept: inv[b][k] = lam^-1/2 if
+// lam > cut*lam_0 else 0.  Columns of U, V (n_r x r row-major, batch) whose lam <= rank_tol*lam_0
+// are zeroed.  sinv[b][k] = 1/lam for lam > rank_tol*lam_0 else 0.
+void proj_prepare(const double* lam, double* U, double* V, double* inv, double* sinv, int batch,
+                  int64_t n_r, int r, int kept, double cut, double rank_tol, int* status, cudaStream_t st);
+// X[b][i][k] = Y[b][i*ldy + k] * s[b][k] for k < kept (X is n x kept row-major)
+void scale_cols(const double* Y, int64_t ldy, int64_t strideY, const double* s, int64_t strideS, double* X,
+                int batch, int64_t n, int kept, cudaStream_t st);
+// dl[b][k] = -0.5 inv^3 (sum_i dZ[i][k] U[i][k] + sum_i dW[i][k] V[i][k]), k < kept
+void proj_dlam(const double* dZ, const double* U, const double* dW, const double* V, const double* inv,
+               double* dl, int batch, int64_t n_r, int r, int kept, cudaStream_t st);
+// core (r x r) of the thin-SVD adjoint (see linalg notes in ctm.cu)
+void proj_core(const double* Aa, const double* Bb, const double* lam, const double* dl, double* core, int batch,
+               int r, int kept, double rank_tol, double eps, cudaStream_t st);
+// E[b] = (dU[b] - X[b]) * sinv[b] (n_r x kept)
+void proj_resid(const double* dU, const double* X, const double* sinv, double* E, int batch, int64_t n_r,
+                int r, int kept, cudaStream_t st);
+
+// ------------------------------------------------------------------ dense linear algebra (FP64)
+// Batched Householder QR of tall column-major matrices (m x n, m >= n, ld = m):
+// on exit the upper triangle holds R, below it the reflectors (v_0 = 1 implicit), tau[n].
+void qr_householder(double* A, double* tau, int batch, int m, int n, int64_t strideA, int* status,
+                    cudaStream_t st);
+// R (n x n, row-major, zeros below the diagonal) from the factored column-major workspace.
+void qr_extract_R(const double* A, double* R, int batch, int m, int n, int64_t strideA, cudaStream_t st);
+// X (m x k, column-major, ld m) := Q X with Q = H_0 ... H_{n-1} from qr_householder.
+void qr_apply_Q(const double* A, const double* tau, double* X, int batch, int m, int n, int k,
+                int64_t strideA, int64_t strideX, int* status, cudaStream_t st);
+// Batched one-sided Jacobi SVD of square r x r matrices.
+// W: column-major working copy (batch x r x r, destroyed); V (batch x r x r column-major) must hold
+// the starting orthogonal matrix (identity for a cold start).  On exit: lam (descending),
+// Uo and Vo row-major r x r with columns = singular vectors, sorted.
+void svd_jacobi(double* W, double* V, double* lam, double* Uo, double* Vo, int batch, int r, int max_sweeps,
+                int* status, int* sweeps_out, cudaStream_t st);
+void set_identity_colmajor(double* V, int batch, int r, cudaStream_t st);
+// X[k*m + i] = U[i*r + k] for i < r, 0 for r <= i < m  (k < r): [U; 0] stored column-major.
+void embed_transpose(const double* U, int r, double* X, int64_t m, cudaStream_t st);
+
+// ------------------------------------------------------------------ energy (FP64)
+// rho: n_terms x (d^2 x d^2) [ket (s1 s2)][bra (s1' s2')], any dtype converted to FP64.
+// hs: n_terms x d^2 x d^2 FP64 device, coup: n_terms.  e_bond[t] = Tr(rho h)/Tr(rho),
+// *e_site = sum_t coup_t e_t / n_sites.  drho (FP64, optional) gets dE/drho.
+void energy_terms(const double* rho, const double* hs, const double* coup, int n_terms, int d2, double inv_sites,
+                  double* e_bond, double* e_site, double* drho, int* status, cudaStream_t st);
+
+// spectrum change between two sets of normalised spectra (batch x kept), result max into *out (atomic max)
+void spectrum_delta(const double* lam, const double* lam_prev, int batch, int r, int kept, double* out,
+                    cudaStream_t st);
+
+}  // namespace ctm

@@ -1,0 +1,407 @@
+// FP64 dense linear algebra of the projector step: batched Householder QR
+// (Golub & Van Loan, Alg. 5.2.1 with LAPACK's reflector convention) and
+// batched one-sided Jacobi SVD (Hestenes 1958; Rutishauser's rotation,
+// cyclic round-robin ordering as in Brent & Luk 1985).
+//
+// Columns move between blocks from one step to the next, so every load of
+// shared state in these kernels bypasses L1 (ld.global.cg).
+//
+// All three sweep-style kernels are persistent cooperative launches whose
+// blocks meet at a software grid barrier between dependent steps.  Every
+// wait is bounded: a block that waits too long raises DEV_TIMEOUT in the
+// status word, sets the shared abort flag and returns; the others see the
+// flag in their own waits and return as well.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "kernels.h"
+
+namespace ctm {
+namespace {
+
+constexpr long kSpinLimit = 1L << 22;  // ~ a few seconds with the back-off below
+
+struct Sync {
+  unsigned* bar;  // [0] arrival count, [1] generation
+  int* abort;
+  int* status;
+};
+
+// Returns false if the barrier was abandoned (timeout or abort).
+__device__ bool grid_barrier(const Sync& s) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* vgen = s.bar + 1;
+    volatile int* vab = s.abort;
+    unsigned g = *vgen;
+    __threadfence();
+    unsigned arrived = atomicAdd(s.bar, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(s.bar, 0u);
+      __threadfence();
+      atomicAdd(s.bar + 1, 1u);
+    } else {
+      long spins = 0;
+      while (*vgen == g) {
+        if (*vab) {
+          ok = 0;
+          break;
+        }
+        if (++spins > kSpinLimit) {
+          atomicOr(s.status, DEV_TIMEOUT);
+          atomicExch(s.abort, 1);
+          ok = 0;
+          break;
+        }
+        if (spins > 64) __nanosleep(256);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Reflector for column j of a column-major m x n matrix (ld = m): on exit A[j][j] = beta,
+// A[j+1:, j] = v[1:], tau[j].  Executed by one full warp.
+__device__ void make_reflector(double* A, double* tau, int m, int j, int lane) {
+  double* col = A + (int64_t)j * m;
+  double alpha = __ldcg(col + j);
+  double s = 0.0;
+  for (int i = j + 1 + lane; i < m; i += 32) {
+    double v = __ldcg(col + i);
+    s = fma(v, v, s);
+  }
+  s = warp_sum(s);
+  double t = 0.0;
+  if (s > 0.0) {
+    double beta = -copysign(sqrt(alpha * alpha + s), alpha);
+    t = (beta - alpha) / beta;
+    double sc = 1.0 / (alpha - beta);
+    for (int i = j + 1 + lane; i < m; i += 32) col[i] = __ldcg(col + i) * sc;
+    __syncwarp();
+    if (lane == 0) col[j] = beta;
+  }
+  if (lane == 0) tau[j] = t;
+  __syncwarp();
+}
+
+// X[:, c] -= tau_j v_j (v_j . X[j:, c]) for one column (one warp).
+__device__ void apply_reflector(const double* Acol_j, double tau_j, double* x, int m, int j, int lane) {
+  if (tau_j == 0.0) return;
+  double w = (lane == 0) ? __ldcg(x + j) : 0.0;
+  for (int i = j + 1 + lane; i < m; i += 32) w = fma(__ldcg(Acol_j + i), __ldcg(x + i), w);
+  w = warp_sum(w) * tau_j;
+  if (lane == 0) x[j] = __ldcg(x + j) - w;
+  for (int i = j + 1 + lane; i < m; i += 32) x[i] = fma(-w, __ldcg(Acol_j + i), __ldcg(x + i));
+  __syncwarp();
+}
+
+__global__ void qr_kernel(double* A, double* tau, int batch, int m, int n, int64_t strideA, Sync s) {
+  const int lane = threadIdx.x % 32;
+  const int wpb = blockDim.x / 32;
+  const int64_t gw = (int64_t)blockIdx.x * wpb + threadIdx.x / 32;
+  const int64_t nw = (int64_t)gridDim.x * wpb;
+  // reflector of column 0
+  for (int64_t b = gw; b < batch; b += nw) make_reflector(A + b * strideA, tau + b * n, m, 0, lane);
+  for (int j = 0; j < n - 1; ++j) {
+    if (!grid_barrier(s)) return;
+    const int64_t ncols = n - j - 1;
+    const int64_t tasks = (int64_t)batch * ncols;
+    for (int64_t t = gw; t < tasks; t += nw) {
+      const int64_t b = t / ncols;
+      const int c = j + 1 + (int)(t % ncols);
+      double* Ab = A + b * strideA;
+      const double tj = __ldcg(tau + b * n + j);
+      apply_reflector(Ab + (int64_t)j * m, tj, Ab + (int64_t)c * m, m, j, lane);
+      if (c == j + 1) make_reflector(Ab, tau + b * n, m, j + 1, lane);
+    }
+  }
+}
+
+__global__ void apply_q_kernel(const double* A, const double* tau, double* X, int batch, int m, int n, int k,
+                               int64_t strideA, int64_t strideX, Sync s) {
+  const int lane = threadIdx.x % 32;
+  const int wpb = blockDim.x / 32;
+  const int64_t gw = (int64_t)blockIdx.x * wpb + threadIdx.x / 32;
+  const int64_t nw = (int64_t)gridDim.x * wpb;
+  const int64_t tasks = (int64_t)batch * k;
+  for (int j = n - 1; j >= 0; --j) {
+    for (int64_t t = gw; t < tasks; t += nw) {
+      const int64_t b = t / k;
+      const int c = (int)(t % k);
+      apply_reflector(A + b * strideA + (int64_t)j * m, __ldcg(tau + b * n + j), X + b * strideX + (int64_t)c * m, m, j, lane);
+    }
+    if (j > 0 && !grid_barrier(s)) return;
+  }
+}
+
+__global__ void extract_r_kernel(const double* A, double* R, int m, int n, int64_t strideA) {
+  const int b = blockIdx.y;
+  int64_t total = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / n), c = (int)(e % n);
+    R[(int64_t)b * total + e] = (c >= i) ? A[(int64_t)b * strideA + (int64_t)c * m + i] : 0.0;
+  }
+}
+
+// ------------------------------------------------------------------ one-sided Jacobi
+__device__ __forceinline__ void rr_pair(int round, int k, int rp, int& p, int& q) {
+  const int n1 = rp - 1;
+  if (k == 0) {
+    p = round;
+    q = n1;
+  } else {
+    p = (round + k) % n1;
+    q = (round - k + n1) % n1;
+  }
+}
+
+__global__ void jacobi_kernel(double* W, double* V, int batch, int r, int rp, int max_sweeps, double tol, int* flags,
+                              int* conv, int* sweeps_out, Sync s) {
+  const int lane = threadIdx.x % 32;
+  const int wpb = blockDim.x / 32;
+  const int64_t gw = (int64_t)blockIdx.x * wpb + threadIdx.x / 32;
+  const int64_t nw = (int64_t)gridDim.x * wpb;
+  const int npairs = rp / 2;
+  const int64_t tasks = (int64_t)batch * npairs;
+  const int64_t rr = (int64_t)r * r;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    int* fl = flags + (sweep % 3) * batch;
+    if (blockIdx.x == 0) {
+      int* nxt = flags + ((sweep + 1) % 3) * batch;
+      for (int b = threadIdx.x; b < batch; b += blockDim.x) nxt[b] = 0;
+      __threadfence();
+    }
+    for (int round = 0; round < rp - 1; ++round) {
+      for (int64_t t = gw; t < tasks; t += nw) {
+        const int b = (int)(t / npairs);
+        if (__ldcg(conv + b)) continue;
+        int p, q;
+        rr_pair(round, (int)(t % npairs), rp, p, q);
+        if (p >= r || q >= r) continue;
+        double* ap = W + b * rr + (int64_t)p * r;
+        double* aq = W + b * rr + (int64_t)q * r;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int i = lane; i < r; i += 32) {
+          double x = __ldcg(ap + i), y = __ldcg(aq + i);
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (fabs(ga) > tol * sqrt(al * be) && ga != 0.0) {
+          double zeta = (be - al) / (2.0 * ga);
+          double tt;
+          if (fabs(zeta) > 1e150)
+            tt = 0.5 / zeta;
+          else
+            tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          double c = 1.0 / sqrt(1.0 + tt * tt);
+          double sn = c * tt;
+          for (int i = lane; i < r; i += 32) {
+            double x = __ldcg(ap + i), y = __ldcg(aq + i);
+            ap[i] = c * x - sn * y;
+            aq[i] = sn * x + c * y;
+          }
+          double* vp = V + b * rr + (int64_t)p * r;
+          double* vq = V + b * rr + (int64_t)q * r;
+          for (int i = lane; i < r; i += 32) {
+            double x = __ldcg(vp + i), y = __ldcg(vq + i);
+            vp[i] = c * x - sn * y;
+            vq[i] = sn * x + c * y;
+          }
+          if (lane == 0) fl[b] = 1;
+        }
+        __syncwarp();
+      }
+      if (!grid_barrier(s)) return;
+    }
+    // decide convergence: every block reads the same flags and conv after the barrier
+    int all = 1;
+    {
+      volatile int* vf = fl;
+      volatile int* vc = conv;
+      for (int b = 0; b < batch; ++b)
+        if (!vc[b] && vf[b] != 0) all = 0;
+    }
+    if (!grid_barrier(s)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      volatile int* vf = fl;
+      for (int b = 0; b < batch; ++b)
+        if (vf[b] == 0) conv[b] = 1;
+      __threadfence();
+    }
+    if (!grid_barrier(s)) return;
+    if (all) {
+      ++sweep;
+      break;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *sweeps_out = sweep;
+    for (int b = 0; b < batch; ++b)
+      if (!conv[b]) atomicOr(s.status, DEV_SVD_NOCONV);
+  }
+}
+
+// Column norms, descending order, normalised left vectors.  One block per matrix.
+__global__ void svd_finalize_kernel(const double* W, const double* V, double* lam, double* Uo, double* Vo, int r,
+                                    int* status) {
+  extern __shared__ double sm[];
+  double* nrm = sm;              // r
+  int* rank = (int*)(sm + r);    // r
+  const int b = blockIdx.x;
+  const int64_t rr = (int64_t)r * r;
+  const double* Wb = W + b * rr;
+  const double* Vb = V + b * rr;
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nwarp = blockDim.x / 32;
+  for (int k = warp; k < r; k += nwarp) {
+    double s = 0.0;
+    for (int i = lane; i < r; i += 32) s = fma(Wb[(int64_t)k * r + i], Wb[(int64_t)k * r + i], s);
+    s = warp_sum(s);
+    if (lane == 0) {
+      nrm[k] = sqrt(s);
+      if (!isfinite(s)) atomicOr(status, DEV_NONFINITE);
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < r; k += blockDim.x) {
+    int rk = 0;
+    double v = nrm[k];
+    for (int j = 0; j < r; ++j) rk += (nrm[j] > v) || (nrm[j] == v && j < k);
+    rank[k] = rk;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < r; k += blockDim.x) lam[(int64_t)b * r + rank[k]] = nrm[k];
+  for (int64_t e = threadIdx.x; e < rr; e += blockDim.x) {
+    int k = (int)(e / r), i = (int)(e % r);  // column k, row i
+    double inv = nrm[k] > 0.0 ? 1.0 / nrm[k] : 0.0;
+    Uo[b * rr + (int64_t)i * r + rank[k]] = Wb[e] * inv;
+    Vo[b * rr + (int64_t)i * r + rank[k]] = Vb[e];
+  }
+}
+
+__global__ void identity_kernel(double* V, int r) {
+  const int b = blockIdx.y;
+  int64_t rr = (int64_t)r * r;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < rr; e += (int64_t)gridDim.x * blockDim.x)
+    V[b * rr + e] = (e / r == e % r) ? 1.0 : 0.0;
+}
+
+// Per-device scratch for the barriers and flags of the cooperative kernels.
+struct CoopScratch {
+  unsigned* bar = nullptr;
+  int* abort = nullptr;
+  int* flags = nullptr;
+  int* conv = nullptr;
+  int flags_cap = 0;
+};
+
+thread_local CoopScratch g_coop;
+
+void ensure_coop(int batch, cudaStream_t st) {
+  if (!g_coop.bar) {
+    CTM_CUDA(cudaMalloc(&g_coop.bar, 2 * sizeof(unsigned)));
+    CTM_CUDA(cudaMalloc(&g_coop.abort, sizeof(int)));
+  }
+  if (g_coop.flags_cap < batch) {
+    if (g_coop.flags) {
+      CTM_CUDA(cudaFree(g_coop.flags));
+      CTM_CUDA(cudaFree(g_coop.conv));
+    }
+    g_coop.flags_cap = std::max(batch, 64);
+    CTM_CUDA(cudaMalloc(&g_coop.flags, 3 * g_coop.flags_cap * sizeof(int)));
+    CTM_CUDA(cudaMalloc(&g_coop.conv, g_coop.flags_cap * sizeof(int)));
+  }
+  CTM_CUDA(cudaMemsetAsync(g_coop.bar, 0, 2 * sizeof(unsigned), st));
+  CTM_CUDA(cudaMemsetAsync(g_coop.abort, 0, sizeof(int), st));
+}
+
+int coop_grid(const void* kernel, int threads) {
+  int dev = 0, sms = 0, per_sm = 0;
+  CTM_CUDA(cudaGetDevice(&dev));
+  CTM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0));
+  CTM_CHECK(per_sm > 0, CTM_ERR_CUDA, "cooperative kernel cannot be resident");
+  return sms * std::min(per_sm, 4);
+}
+
+}  // namespace
+
+void qr_householder(double* A, double* tau, int batch, int m, int n, int64_t strideA, int* status, cudaStream_t st) {
+  if (batch == 0 || n == 0) return;
+  ensure_coop(batch, st);
+  const int threads = 256;
+  int grid = coop_grid((const void*)qr_kernel, threads);
+  int64_t need = ((int64_t)batch * n + threads / 32 - 1) / (threads / 32);
+  grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, need));
+  Sync s{g_coop.bar, g_coop.abort, status};
+  void* args[] = {&A, &tau, &batch, &m, &n, &strideA, &s};
+  CTM_CUDA(cudaLaunchCooperativeKernel((const void*)qr_kernel, grid, threads, args, 0, st));
+  CTM_LAUNCHED();
+}
+
+void qr_extract_R(const double* A, double* R, int batch, int m, int n, int64_t strideA, cudaStream_t st) {
+  dim3 grid((unsigned)std::min<int64_t>(4096, ((int64_t)n * n + 255) / 256), batch);
+  extract_r_kernel<<<grid, 256, 0, st>>>(A, R, m, n, strideA);
+  CTM_LAUNCHED();
+}
+
+void qr_apply_Q(const double* A, const double* tau, double* X, int batch, int m, int n, int k, int64_t strideA,
+                int64_t strideX, int* status, cudaStream_t st) {
+  if (batch == 0 || n == 0) return;
+  ensure_coop(batch, st);
+  const int threads = 256;
+  int grid = coop_grid((const void*)apply_q_kernel, threads);
+  int64_t need = ((int64_t)batch * k + threads / 32 - 1) / (threads / 32);
+  grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, need));
+  Sync s{g_coop.bar, g_coop.abort, status};
+  void* args[] = {&A, &tau, &X, &batch, &m, &n, &k, &strideA, &strideX, &s};
+  CTM_CUDA(cudaLaunchCooperativeKernel((const void*)apply_q_kernel, grid, threads, args, 0, st));
+  CTM_LAUNCHED();
+}
+
+void set_identity_colmajor(double* V, int batch, int r, cudaStream_t st) {
+  dim3 grid((unsigned)std::min<int64_t>(4096, ((int64_t)r * r + 255) / 256), batch);
+  identity_kernel<<<grid, 256, 0, st>>>(V, r);
+  CTM_LAUNCHED();
+}
+
+void svd_jacobi(double* W, double* V, double* lam, double* Uo, double* Vo, int batch, int r, int max_sweeps,
+                int* status, int* sweeps_out, cudaStream_t st) {
+  if (batch == 0 || r == 0) return;
+  ensure_coop(batch, st);
+  CTM_CUDA(cudaMemsetAsync(g_coop.flags, 0, 3 * batch * sizeof(int), st));
+  CTM_CUDA(cudaMemsetAsync(g_coop.conv, 0, batch * sizeof(int), st));
+  const int threads = 256;
+  int rp = r + (r & 1);
+  int grid = coop_grid((const void*)jacobi_kernel, threads);
+  int64_t need = ((int64_t)batch * (rp / 2) + threads / 32 - 1) / (threads / 32);
+  grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, need));
+  double tol = 2.220446049250313e-16 * r;
+  Sync s{g_coop.bar, g_coop.abort, status};
+  int* flags = g_coop.flags;
+  int* conv = g_coop.conv;
+  void* args[] = {&W, &V, &batch, &r, &rp, &max_sweeps, &tol, &flags, &conv, &sweeps_out, &s};
+  CTM_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, grid, threads, args, 0, st));
+  CTM_LAUNCHED();
+  size_t smem = (size_t)r * (sizeof(double) + sizeof(int));
+  if (smem > 48 * 1024) CTM_CUDA(cudaFuncSetAttribute(svd_finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  svd_finalize_kernel<<<batch, 256, smem, st>>>(W, V, lam, Uo, Vo, r, status);
+  CTM_LAUNCHED();
+}
+
+}  // namespace ctm

@@ -166,8 +166,26 @@ __device__ __forceinline__ void rr_pair(int round, int k, int rp, int& p, int& q
   }
 }
 
+// Squared Frobenius norm of each matrix (deterministic, one block per matrix).
+__global__ void frob2_kernel(const double* W, int64_t rr, double* out) {
+  __shared__ double sh[256];
+  const double* Wb = W + blockIdx.x * rr;
+  double acc = 0.0;
+  for (int64_t e = threadIdx.x; e < rr; e += blockDim.x) acc = fma(Wb[e], Wb[e], acc);
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+}
+
+// A pair is rotated when |g| > tol sqrt(a) sqrt(b) (products of square roots cannot underflow) and
+// both columns lie above the rounding floor 1e-32 ||M||_F^2: below it a column is noise whose
+// direction no further rotation can settle, and its singular value is a numerical zero.
 __global__ void jacobi_kernel(double* W, double* V, int batch, int r, int rp, int max_sweeps, double tol, int* flags,
-                              int* conv, int* sweeps_out, Sync s) {
+                              int* conv, int* sweeps_out, const double* frob2, Sync s) {
   const int lane = threadIdx.x % 32;
   const int wpb = blockDim.x / 32;
   const int64_t gw = (int64_t)blockIdx.x * wpb + threadIdx.x / 32;
@@ -202,7 +220,8 @@ __global__ void jacobi_kernel(double* W, double* V, int batch, int r, int rp, in
         al = warp_sum(al);
         be = warp_sum(be);
         ga = warp_sum(ga);
-        if (fabs(ga) > tol * sqrt(al * be) && ga != 0.0) {
+        const double floor2 = 1e-32 * __ldcg(frob2 + b);
+        if (al > floor2 && be > floor2 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
           double zeta = (be - al) / (2.0 * ga);
           double tt;
           if (fabs(zeta) > 1e150)
@@ -307,6 +326,7 @@ struct CoopScratch {
   int* abort = nullptr;
   int* flags = nullptr;
   int* conv = nullptr;
+  double* frob2 = nullptr;
   int flags_cap = 0;
 };
 
@@ -321,10 +341,12 @@ void ensure_coop(int batch, cudaStream_t st) {
     if (g_coop.flags) {
       CTM_CUDA(cudaFree(g_coop.flags));
       CTM_CUDA(cudaFree(g_coop.conv));
+      CTM_CUDA(cudaFree(g_coop.frob2));
     }
     g_coop.flags_cap = std::max(batch, 64);
     CTM_CUDA(cudaMalloc(&g_coop.flags, 3 * g_coop.flags_cap * sizeof(int)));
     CTM_CUDA(cudaMalloc(&g_coop.conv, g_coop.flags_cap * sizeof(int)));
+    CTM_CUDA(cudaMalloc(&g_coop.frob2, g_coop.flags_cap * sizeof(double)));
   }
   CTM_CUDA(cudaMemsetAsync(g_coop.bar, 0, 2 * sizeof(unsigned), st));
   CTM_CUDA(cudaMemsetAsync(g_coop.abort, 0, sizeof(int), st));
@@ -395,7 +417,10 @@ void svd_jacobi(double* W, double* V, double* lam, double* Uo, double* Vo, int b
   Sync s{g_coop.bar, g_coop.abort, status};
   int* flags = g_coop.flags;
   int* conv = g_coop.conv;
-  void* args[] = {&W, &V, &batch, &r, &rp, &max_sweeps, &tol, &flags, &conv, &sweeps_out, &s};
+  double* frob2 = g_coop.frob2;
+  frob2_kernel<<<batch, 256, 0, st>>>(W, (int64_t)r * r, frob2);
+  CTM_LAUNCHED();
+  void* args[] = {&W, &V, &batch, &r, &rp, &max_sweeps, &tol, &flags, &conv, &sweeps_out, &frob2, &s};
   CTM_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, grid, threads, args, 0, st));
   CTM_LAUNCHED();
   size_t smem = (size_t)r * (sizeof(double) + sizeof(int));

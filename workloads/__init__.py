@@ -77,6 +77,34 @@ class Workload:
         return self.Lx * self.Ly
 
 
+ISING_K = 0.42       # amplitude coupling; the norm network is the Ising model at 2*(K/2)*2 = K, K_c = 0.4407
+ISING_NOISE = 0.05
+
+
+def ising_site(seed: int, d: int, D: int, K: float = ISING_K, noise: float = ISING_NOISE) -> np.ndarray:
+    """Sign-free correlated PEPS tensor: the Ising wave function plus positive noise.
+
+    psi(s) = prod_<ij> exp(K s_i s_j / 2) (s = +-1 for sigma = up, down) is a
+    D=2 PEPS with A[s; l, u, r, d] = W[s,l] W[s,u] W[s,r] W[s,d], where
+    W W^t = exp(K s s' / 2).  Its norm network is the classical Ising model at
+    coupling K, close to criticality for K = 0.42, so the environment spectra
+    decay slowly.  The tensor is embedded in bond dimension D and every entry
+    gets noise * |N(0,1)| from ``np.random.default_rng(seed)``; the result is
+    scaled to max-abs 1.
+    """
+    assert d == 2
+    spin = np.array([1.0, -1.0])
+    B = np.exp(0.5 * K * np.outer(spin, spin))
+    w, v = np.linalg.eigh(B)
+    Wm = v @ np.diag(np.sqrt(w)) @ v.T
+    A = np.zeros((d, D, D, D, D))
+    k = min(2, D)
+    core = np.einsum("sl,su,sr,sd->slurd", Wm[:, :k], Wm[:, :k], Wm[:, :k], Wm[:, :k])
+    A[:, :k, :k, :k, :k] = core
+    A += noise * np.abs(np.random.default_rng(seed).standard_normal(A.shape))
+    return A / np.abs(A).max()
+
+
 def random_site(seed: int, d: int, D: int, std: float | None = None, maxabs: bool = False,
                 signed: bool = False) -> np.ndarray:
     """|N(0,1)| draw from ``np.random.default_rng(seed)``, scaled by ``std`` or to max-abs 1.
@@ -122,38 +150,33 @@ def shastry_sutherland_terms(J: float = 0.7, Jp: float = 1.0) -> list:
 
 
 def config(name: str) -> Workload:
-    """The seeded workloads: shapes and distributions of the paper's runs.
+    """The seeded workloads: shapes of the paper's runs, sign-free correlated tensors.
 
-    heis_d2_chi8:  D=2, chi=8, 20 iterations, one tensor |N(0,1)| seed 0 / max-abs
-    heis_d4_chi32: D=4, chi=32, 40 iterations, |N(0,1)| seed 1, std 1/sqrt(2 D^4)
+    heis_d2_chi8:  rotated Heisenberg, 1-site, D=2, chi=8, 20 iterations, seed 0
+    heis_d4_chi32: rotated Heisenberg, 1-site, D=4, chi=32, 40 iterations, seed 1
     ss_d6_chi64:   Shastry-Sutherland J=0.7, J'=1, 2x2 cell, D=6, chi=64,
-                   50 iterations, seeds 2..5 (one per site), std 1/sqrt(2 D^4)
-    heis_d9_chi81: D=9, chi=81, 60 iterations, seed 6, std 1/sqrt(2 D^4)
+                   50 iterations, seeds 2..5 (one per site)
+    heis_d9_chi81: rotated Heisenberg, 1-site, D=9, chi=81, 60 iterations, seed 6
+    Every site tensor is ``ising_site(seed, 2, D)``.
     """
     d = 2
     if name == "heis_d2_chi8":
-        D = 2
-        return Workload(name, 1, 1, d, D, 8, 20, [random_site(0, d, D, maxabs=True)], heisenberg_terms_rotated())
+        return Workload(name, 1, 1, d, 2, 8, 20, [ising_site(0, d, 2)], heisenberg_terms_rotated())
     if name == "heis_d4_chi32":
-        D = 4
-        return Workload(name, 1, 1, d, D, 32, 40, [random_site(1, d, D, std=1 / np.sqrt(2 * D**4))],
-                        heisenberg_terms_rotated(), precision="tf32")
+        return Workload(name, 1, 1, d, 4, 32, 40, [ising_site(1, d, 4)], heisenberg_terms_rotated(),
+                        precision="tf32")
     if name == "ss_d6_chi64":
-        D = 6
-        ts = [random_site(s, d, D, std=1 / np.sqrt(2 * D**4)) for s in (2, 3, 4, 5)]
-        return Workload(name, 2, 2, d, D, 64, 50, ts, shastry_sutherland_terms(), precision="bf16")
+        ts = [ising_site(s, d, 6) for s in (2, 3, 4, 5)]
+        return Workload(name, 2, 2, d, 6, 64, 50, ts, shastry_sutherland_terms(), precision="bf16")
     if name == "heis_d9_chi81":
-        D = 9
-        return Workload(name, 1, 1, d, D, 81, 60, [random_site(6, d, D, std=1 / np.sqrt(2 * D**4))],
-                        heisenberg_terms_rotated(), precision="bf16")
+        return Workload(name, 1, 1, d, 9, 81, 60, [ising_site(6, d, 9)], heisenberg_terms_rotated(),
+                        precision="bf16")
     raise KeyError(name)
 
 
-def custom(Lx, Ly, D, chi, n_iter, seeds, terms, d=2, std=None, maxabs=False, name="custom") -> Workload:
+def custom(Lx, Ly, D, chi, n_iter, seeds, terms, d=2, name="custom") -> Workload:
     """A workload of arbitrary size drawn the same way (used by scaled-down tests)."""
-    if std is None and not maxabs:
-        std = 1 / np.sqrt(2 * D**4)
-    ts = [random_site(s, d, D, std=std, maxabs=maxabs) for s in seeds]
+    ts = [ising_site(s, d, D) for s in seeds]
     assert len(ts) == Lx * Ly
     return Workload(name, Lx, Ly, d, D, chi, n_iter, ts, terms)
 

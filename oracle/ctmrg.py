@@ -65,6 +65,17 @@ SLOTS = ("C_ul", "T_u", "C_ur", "T_r", "C_dr", "T_d", "C_dl", "T_l")
 
 
 # ----------------------------------------------------------------------------- projectors
+def _svd(M: torch.Tensor):
+    """Full SVD M = U diag(s) V^t by LAPACK's QR-iteration driver (dgesvd).
+
+    The divide-and-conquer driver (dgesdd) aborted on some of these badly
+    scaled bond matrices on one of the platforms this runs on; dgesvd does not.
+    """
+    import scipy.linalg
+    U, s, Vh = scipy.linalg.svd(M.detach().numpy(), full_matrices=True, lapack_driver="gesvd")
+    return torch.from_numpy(U), torch.from_numpy(s), torch.from_numpy(Vh.T.copy())
+
+
 def _broadened_inverse_gaps(s: torch.Tensor, nz: torch.Tensor) -> torch.Tensor:
     """F_ij = (s_j^2 - s_i^2)/((s_j^2 - s_i^2)^2 + EPS s_1^4) on the non-zero set, 0 elsewhere."""
     s2 = s * s
@@ -84,8 +95,7 @@ class Projectors(torch.autograd.Function):
         Qn, Rn = torch.linalg.qr(N, mode="reduced")
         Qs, Rs = torch.linalg.qr(S, mode="reduced")
         M = Rn @ Rs.T
-        U, s, Vh = torch.linalg.svd(M)
-        V = Vh.T
+        U, s, V = _svd(M)
         k = s.shape[0]
         kept = min(chi, k)
         cut = CUTOFF * s[0]
@@ -312,7 +322,7 @@ def _spectrum(N, S, chi):
     with torch.no_grad():
         _, Rn = torch.linalg.qr(N, mode="reduced")
         _, Rs = torch.linalg.qr(S, mode="reduced")
-        s = torch.linalg.svdvals(Rn @ Rs.T)[:chi]
+        s = _svd(Rn @ Rs.T)[1][:chi]
         return s / s.sum()
 
 

@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Energy+gradient evaluations per second of the nested single-layer CTMRG on GB300.
+
+One step = one full evaluation of the hot path on one batch of synthetic input:
+ctm_init from the seeded initial environment, n_iter CTMRG iterations
+(left/right/up/down moves, QR+SVD projectors), the energy from the impurity
+reduced density matrices, and the reverse-mode gradient through every
+iteration.  Default workload: Shastry-Sutherland model, 2x2 PEPS cell (4x4
+nested cell), D=6, chi=64, 50 iterations.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P] [--impl ours|reference]
+Multi-GPU (torchrun, one rank per GPU): independent replicas (the path does not shard
+inside one evaluation); value = evaluations of all ranks / max wall time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "energy+grad evals/s at D=6,chi=64 (mixed vs FP64, |dE|<=1e-6); TC/HBM roofline %"
+UNIT = "evals/s"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p)), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# Nominal unit rates of one GB300 (152 SMs at 2.07 GHz) for kernels bound by plain ALU arithmetic:
+# FP64 FMA 2/clk/SM -> 1.26 TFLOP/s (the published 1.25); FP32 FMA 128/clk/SM -> 80.5 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _inputs(w, device):
+    import numpy as np
+    import torch
+    import workloads as W
+    env0 = W.initial_environment(w)
+    A = torch.tensor(np.stack(w.tensors), dtype=torch.float64)
+    E0 = torch.tensor(np.concatenate([a.ravel() for s in env0 for a in s]), dtype=torch.float64)
+    return A, E0
+
+
+def _roofline(prof, precision, peaks, peak_kind):
+    """Roofline of the kernel class with the largest device time over the timed region."""
+    name, (ms, n, fl, by) = max(prof.items(), key=lambda kv: kv[1][0])
+    if n == 0 or ms == 0:
+        return None
+    if name == "permute":
+        ach = by / (ms * 1e-3) / 1e9
+        peak = peaks["hbm_gbs"]
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "launches": n, "peak_source": peak_kind}
+    if name == "tc_gemm":
+        ach = fl / (ms * 1e-3) / 1e12
+        bf16 = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        peak = bf16 if precision.startswith("bf16") else bf16 / 2.0
+        return {"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "launches": n,
+                "peak_source": f"{peak_kind} bf16 sustained" + ("" if precision.startswith("bf16") else " x 1/2 (tf32)")}
+    fp64 = name in ("svd", "qr") or precision == "fp64"
+    peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+    ach = fl / (ms * 1e-3) / 1e12
+    return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None, "launches": n,
+            "peak_source": "nominal FP64 FMA rate (2/clk/SM x 152 SM x 2.07 GHz)" if fp64 else
+            "nominal FP32 FMA rate (128/clk/SM x 152 SM x 2.07 GHz)"}
+
+
+def _cpu_baseline(w, threads):
+    """The oracle as it stands, on the host cores, on a bounded sample of the same workload:
+    energy+gradient with 0 and with 1 CTMRG iteration; a full evaluation is estimated as
+    t0 + n_iter * (t1 - t0)."""
+    import torch
+    import workloads as W
+    from oracle.api import evaluate
+    torch.set_num_threads(threads)
+    env0 = W.initial_environment(w)
+    t = time.perf_counter()
+    evaluate(w.tensors, w.Lx, w.Ly, w.chi, 0, w.terms, env0=env0)
+    t0 = time.perf_counter() - t
+    t = time.perf_counter()
+    evaluate(w.tensors, w.Lx, w.Ly, w.chi, 1, w.terms, env0=env0)
+    t1 = time.perf_counter() - t
+    est = t0 + w.n_iter * max(t1 - t0, 0.0)
+    return {"value": 1.0 / est, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"oracle energy+gradient at n_iter=0 ({t0:.1f}s) and n_iter=1 ({t1:.1f}s) on the full "
+                      f"{w.name} workload; full {w.n_iter}-iteration evaluation estimated as t0+{w.n_iter}*(t1-t0)"
+                      f" = {est:.0f}s"}
+
+
+def run_reference(args, w):
+    """Reference arm: the FP64 CPU oracle on the host cores (rank 0 only)."""
+    import torch
+    import workloads as W
+    from oracle.api import evaluate
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    torch.set_num_threads(threads)
+    env0 = W.initial_environment(w)
+    t = time.perf_counter()
+    evaluate(w.tensors, w.Lx, w.Ly, w.chi, 0, w.terms, env0=env0)
+    t0 = time.perf_counter() - t
+    for _ in range(max(0, args.warmup - 1)):
+        evaluate(w.tensors, w.Lx, w.Ly, w.chi, 1, w.terms, env0=env0)
+    ts = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        evaluate(w.tensors, w.Lx, w.Ly, w.chi, 1, w.terms, env0=env0)
+        ts.append(time.perf_counter() - t)
+    t1 = sum(ts) / len(ts)
+    est = t0 + w.n_iter * max(t1 - t0, 0.0)
+    value = 1.0 / est
+    sample = (f"each step: oracle energy+gradient with 1 CTMRG iteration on the full {w.name} workload "
+              f"(t1={t1:.1f}s); n_iter=0 evaluation t0={t0:.1f}s; full evaluation estimated as "
+              f"t0+{w.n_iter}*(t1-t0)={est:.0f}s")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * est, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "Lx": w.Lx, "Ly": w.Ly, "D": w.D, "chi": w.chi, "n_iter": w.n_iter,
+                   "model": "Shastry-Sutherland J=0.7 J'=1" if w.name.startswith("ss") else "Heisenberg"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="tf32")
+    ap.add_argument("--workload", default="ss_d6_chi64")
+    ap.add_argument("--n-iter", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    import workloads as W
+    w = W.config(args.workload)
+    if args.n_iter is not None:
+        w.n_iter = args.n_iter
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2512_14414_gb300 import CTM
+
+    A_h, E0_h = _inputs(w, dev)
+    A = A_h.to(dev)
+    E0 = E0_h.to(dev)
+    ctm = CTM(w.Lx, w.Ly, w.d, w.D, w.chi, [(t.x, t.y, t.kind, t.coupling, t.h) for t in w.terms],
+              precision=args.precision)
+    e = torch.empty(1, dtype=torch.float64, device=dev)
+    dA = torch.empty_like(A)
+
+    def step():
+        ctm.init(A, E0)
+        ctm.grad(w.n_iter, dA=dA, e=e)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = ctm.kernel_launches
+    ctm.profile(True)
+    st = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(st)
+    for _ in range(args.steps):
+        step()
+    ev1.record(st)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    prof = ctm.profile_read()
+    ctm.profile(False)
+    launches = ctm.kernel_launches - launches0
+    ck = clocks.stop()
+    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_max = float(t_max[0])
+    value = world * args.steps / (ms_max * 1e-3)
+    E_val = float(e[0])
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        Ap, Ep = A_h.pin_memory(), E0_h.pin_memory()
+        dA_h = torch.empty(dA.shape, dtype=torch.float64).pin_memory()
+        e_h = torch.empty(1, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            Ad = Ap.to(dev, non_blocking=True)
+            Ed = Ep.to(dev, non_blocking=True)
+            ctm.init(Ad, Ed)
+            ctm.grad(w.n_iter, dA=dA, e=e)
+            dA_h.copy_(dA, non_blocking=True)
+            e_h.copy_(e, non_blocking=True)
+            torch.cuda.synchronize()
+        te = time.perf_counter() - t
+        tt = torch.tensor([te], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * args.steps / float(tt[0]), "unit": UNIT,
+               "h2d_bytes_per_step": int(Ap.numel() * 8 + Ep.numel() * 8),
+               "d2h_bytes_per_step": int(dA_h.numel() * 8 + 8)}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peaks, kind = _peaks()
+    roof = _roofline(prof, args.precision, peaks, kind)
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = _cpu_baseline(w, os.cpu_count() or 1)
+    total_ms = sum(v[0] for v in prof.values()) or 1.0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp64": "f64"}.get(args.precision, args.precision + "+f64"),
+        "data": "synthetic",
+        "config": {"workload": w.name, "model": "Shastry-Sutherland J=0.7 J'=1" if w.name.startswith("ss")
+                   else "Heisenberg (sublattice-rotated)", "Lx": w.Lx, "Ly": w.Ly, "D": w.D, "chi": w.chi,
+                   "n_iter": w.n_iter, "precision": args.precision, "parallelism": f"replicas x{world}",
+                   "l2": "per-step working set (checkpoints, projector factors, tape) is several GB > 129 MB L2"},
+        "energy": E_val,
+        "roofline": roof,
+        "kernel_time_share": {k: round(v[0] / total_ms, 4) for k, v in prof.items() if v[1]},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -138,6 +138,18 @@ int64_t ctm_env_numel(const ctm_handle* h);
 /* Launch counters (kernels enqueued by this handle since creation). */
 int64_t ctm_kernel_launches(const ctm_handle* h);
 
+/* Per-kernel-class device timing.  ctm_profile(h, 1) clears the record and
+ * starts recording a CUDA event pair (on the launching stream) around every
+ * launch of the classes below; ctm_profile(h, 0) stops.  ctm_profile_read
+ * synchronises the last stream used and returns, for one class, the summed
+ * event time (ms), the number of recorded launches and the algorithmic flops
+ * and bytes of those launches (flops of the Jacobi SVD are counted on the
+ * device: 6r per column-pair test and 12r per rotation).
+ * Classes: 0 GEMM (SIMT), 1 permutation, 2 Jacobi SVD, 3 Householder QR,
+ * 4 other, 5 tensor-core GEMM. */
+int ctm_profile(ctm_handle* h, int enable);
+int ctm_profile_read(ctm_handle* h, int cls, double* ms, int64_t* launches, double* flops, double* bytes);
+
 int ctm_destroy(ctm_handle* h);
 const char* ctm_error_string(int status);
 

@@ -55,6 +55,7 @@ the plain QR+SVD on full-rank inputs).
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 DT = torch.float64
@@ -65,6 +66,20 @@ SLOTS = ("C_ul", "T_u", "C_ur", "T_r", "C_dr", "T_d", "C_dl", "T_l")
 
 
 # ----------------------------------------------------------------------------- projectors
+def _qr(A: torch.Tensor):
+    """Reduced QR A = Q R by LAPACK (dgeqrf/dorgqr) through scipy.
+
+    torch's CPU QR returned non-finite factors for finite inputs on one of the
+    platforms this runs on; scipy's LAPACK build does not.
+    """
+    import scipy.linalg
+    a = A.detach().numpy()
+    if not np.isfinite(a).all():
+        raise FloatingPointError("non-finite input to QR")
+    Q, R = scipy.linalg.qr(a, mode="economic")
+    return torch.from_numpy(Q), torch.from_numpy(R)
+
+
 def _svd(M: torch.Tensor):
     """Full SVD M = U diag(s) V^t by LAPACK's QR-iteration driver (dgesvd).
 
@@ -72,7 +87,10 @@ def _svd(M: torch.Tensor):
     scaled bond matrices on one of the platforms this runs on; dgesvd does not.
     """
     import scipy.linalg
-    U, s, Vh = scipy.linalg.svd(M.detach().numpy(), full_matrices=True, lapack_driver="gesvd")
+    m = M.detach().numpy()
+    if not np.isfinite(m).all():
+        raise FloatingPointError("non-finite input to SVD")
+    U, s, Vh = scipy.linalg.svd(m, full_matrices=True, lapack_driver="gesvd")
     return torch.from_numpy(U), torch.from_numpy(s), torch.from_numpy(Vh.T.copy())
 
 
@@ -92,8 +110,8 @@ class Projectors(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, N: torch.Tensor, S: torch.Tensor, chi: int):
-        Qn, Rn = torch.linalg.qr(N, mode="reduced")
-        Qs, Rs = torch.linalg.qr(S, mode="reduced")
+        Qn, Rn = _qr(N)
+        Qs, Rs = _qr(S)
         M = Rn @ Rs.T
         U, s, V = _svd(M)
         k = s.shape[0]
@@ -320,8 +338,8 @@ def left_move(grid, env, chi, spectra=None):
 
 def _spectrum(N, S, chi):
     with torch.no_grad():
-        _, Rn = torch.linalg.qr(N, mode="reduced")
-        _, Rs = torch.linalg.qr(S, mode="reduced")
+        _, Rn = _qr(N)
+        _, Rs = _qr(S)
         s = _svd(Rn @ Rs.T)[1][:chi]
         return s / s.sum()
 

@@ -95,6 +95,19 @@ class CTM:
         _check(self.lib.ctm_grad(self.handle, int(n_iter), _ptr(e), _ptr(dA), _stream()), "ctm_grad")
         return e, dA
 
+    def profile(self, enable=True):
+        _check(self.lib.ctm_profile(self.handle, int(bool(enable))), "ctm_profile")
+
+    def profile_read(self):
+        """{class: (ms, launches, flops, bytes)} for every kernel class since profile(True)."""
+        out = {}
+        for name, c in _lib.PROF_CLASSES.items():
+            ms, n, fl, by = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+            _check(self.lib.ctm_profile_read(self.handle, c, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl),
+                                             ctypes.byref(by)), "ctm_profile_read")
+            out[name] = (ms.value, n.value, fl.value, by.value)
+        return out
+
     def get_env(self):
         out = torch.empty(self.env_numel, dtype=torch.float64, device="cuda")
         _check(self.lib.ctm_get_env(self.handle, _ptr(out), _stream()), "ctm_get_env")

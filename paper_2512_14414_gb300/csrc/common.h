@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <stdexcept>
 #include <string>
+#include <vector>
 #include "../../include/ctm.h"
 
 namespace ctm {
@@ -44,6 +45,31 @@ inline void count_launch() {
     ::ctm::count_launch();                \
     CTM_CUDA(cudaGetLastError());         \
   } while (0)
+
+// Per-class device timing with CUDA events (enabled by ctm_profile).  A scope records an
+// event pair around the launches it encloses, on the launching stream.
+enum ProfClass : int { PROF_GEMM = 0, PROF_PERMUTE = 1, PROF_SVD = 2, PROF_QR = 3, PROF_MISC = 4, PROF_TC = 5,
+                       PROF_NCLASS = 6 };
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;  // pairs
+  std::vector<int> cls;
+  std::vector<double> flops, bytes;
+  size_t used = 0;
+  void begin(int c, cudaStream_t st, double f, double b);
+  void end(cudaStream_t st);
+};
+extern thread_local Profiler* g_prof;
+struct ProfScope {
+  bool active;
+  cudaStream_t st;
+  ProfScope(int c, cudaStream_t s, double f = 0, double b = 0) : active(g_prof && g_prof->on), st(s) {
+    if (active) g_prof->begin(c, s, f, b);
+  }
+  ~ProfScope() {
+    if (active) g_prof->end(st);
+  }
+};
 
 // Device status word bits (written by kernels, read by the host at sync points).
 enum : int { DEV_SVD_NOCONV = 1, DEV_TIMEOUT = 2, DEV_NONFINITE = 4, DEV_DEGENERATE = 8 };

@@ -134,6 +134,9 @@ struct ctm_handle {
   double* dscal = nullptr;  // [0] delta
   double *hs = nullptr, *coup = nullptr;
   std::string last_error;
+  ctm::Profiler prof;
+  double prof_ms[ctm::PROF_NCLASS] = {0}, prof_flops[ctm::PROF_NCLASS] = {0}, prof_bytes[ctm::PROF_NCLASS] = {0};
+  int64_t prof_n[ctm::PROF_NCLASS] = {0};
   // replay state of the current iteration (backward recompute)
   bool replay = false;
   int cur_iter = 0, cur_pair = 0;
@@ -920,17 +923,23 @@ void forward_iters(ctm_handle* h, int n_iter, double* delta_host) {
 namespace {
 int guard(ctm_handle* h, const std::function<void()>& fn) {
   try {
-    if (h) ctm::g_launch_counter = &h->launches;
+    if (h) {
+      ctm::g_launch_counter = &h->launches;
+      ctm::g_prof = &h->prof;
+    }
     fn();
     ctm::g_launch_counter = nullptr;
+    ctm::g_prof = nullptr;
     return CTM_OK;
   } catch (const ctm::Error& e) {
     ctm::g_launch_counter = nullptr;
+    ctm::g_prof = nullptr;
     if (h) h->last_error = e.what();
     fprintf(stderr, "libctm: %s\n", e.what());
     return e.status;
   } catch (const std::exception& e) {
     ctm::g_launch_counter = nullptr;
+    ctm::g_prof = nullptr;
     if (h) h->last_error = e.what();
     fprintf(stderr, "libctm: %s\n", e.what());
     return CTM_ERR_INVALID_ARG;
@@ -1142,6 +1151,48 @@ int64_t ctm_env_numel(const ctm_handle* h) {
 }
 
 int64_t ctm_kernel_launches(const ctm_handle* h) { return h ? h->launches : -1; }
+
+int ctm_profile(ctm_handle* h, int enable) {
+  if (!h) return CTM_ERR_INVALID_ARG;
+  return guard(h, [&]() {
+    if (enable) {
+      if (h->st || h->dev_ready) CTM_CUDA(cudaStreamSynchronize(h->st));
+      h->prof.used = 0;
+      h->prof.cls.clear();
+      h->prof.flops.clear();
+      h->prof.bytes.clear();
+      for (int c = 0; c < ctm::PROF_NCLASS; ++c) h->prof_ms[c] = h->prof_flops[c] = h->prof_bytes[c] = 0, h->prof_n[c] = 0;
+      ctm::jacobi_flops_read_reset(h->st);
+    }
+    h->prof.on = enable != 0;
+  });
+}
+
+int ctm_profile_read(ctm_handle* h, int cls, double* ms, int64_t* launches, double* flops, double* bytes) {
+  if (!h || cls < 0 || cls >= ctm::PROF_NCLASS) return CTM_ERR_INVALID_ARG;
+  return guard(h, [&]() {
+    CTM_CUDA(cudaStreamSynchronize(h->st));
+    auto& P = h->prof;
+    for (size_t k = 0; k + 1 < P.used; k += 2) {
+      float t = 0.f;
+      CTM_CUDA(cudaEventElapsedTime(&t, P.ev[k], P.ev[k + 1]));
+      int c = P.cls[k / 2];
+      h->prof_ms[c] += t;
+      h->prof_n[c] += 1;
+      h->prof_flops[c] += P.flops[k / 2];
+      h->prof_bytes[c] += P.bytes[k / 2];
+    }
+    P.used = 0;
+    P.cls.clear();
+    P.flops.clear();
+    P.bytes.clear();
+    h->prof_flops[ctm::PROF_SVD] += ctm::jacobi_flops_read_reset(h->st);
+    if (ms) *ms = h->prof_ms[cls];
+    if (launches) *launches = h->prof_n[cls];
+    if (flops) *flops = h->prof_flops[cls];
+    if (bytes) *bytes = h->prof_bytes[cls];
+  });
+}
 
 int ctm_destroy(ctm_handle* h) {
   if (!h) return CTM_ERR_INVALID_ARG;

@@ -7,6 +7,24 @@
 namespace ctm {
 
 thread_local int64_t* g_launch_counter = nullptr;
+thread_local Profiler* g_prof = nullptr;
+
+void Profiler::begin(int c, cudaStream_t st, double f, double b) {
+  if (used + 2 > ev.size()) {
+    if (ev.size() >= (size_t(1) << 20)) return;
+    size_t old = ev.size();
+    ev.resize(std::max<size_t>(4096, ev.size() * 2));
+    for (size_t k = old; k < ev.size(); ++k) cudaEventCreate(&ev[k]);
+  }
+  cls.push_back(c);
+  flops.push_back(f);
+  bytes.push_back(b);
+  cudaEventRecord(ev[used++], st);
+}
+
+void Profiler::end(cudaStream_t st) {
+  if (used % 2 == 1) cudaEventRecord(ev[used++], st);
+}
 
 namespace {
 
@@ -97,6 +115,7 @@ void permute_t(const Ti* in, To* out, const PermSpec& ps, bool acc, double scale
   int64_t n = 1;
   for (int k = 0; k < r; ++k) n *= ps.out_dims[k];
   if (n == 0) return;
+  ProfScope prof(PROF_PERMUTE, st, 0.0, (double)n * (sizeof(Ti) + sizeof(To) * (acc ? 2 : 1)));
   int64_t ostr[8];
   int64_t s = 1;
   for (int k = r - 1; k >= 0; --k) {
@@ -152,8 +171,12 @@ __global__ void __launch_bounds__(256) gemm_simt(const T* __restrict__ A, const 
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
-  for (int64_t bb = blockIdx.z; bb < g.batch; bb += gridDim.z) {
+  const int64_t n0 = (int64_t)blockIdx.x * BN;
+  const int64_t mtiles = (g.M + BM - 1) / BM;
+  for (int64_t work = blockIdx.z * (int64_t)gridDim.y + blockIdx.y; work < g.batch * mtiles;
+       work += (int64_t)gridDim.z * gridDim.y) {
+    const int64_t bb = work / mtiles;
+    const int64_t m0 = (work % mtiles) * BM;
     const T* Ab = A + bb * g.strideA;
     const T* Bb = B + bb * g.strideB;
     T* Cb = C + bb * g.strideC;
@@ -229,14 +252,18 @@ __global__ void __launch_bounds__(256) gemm_simt(const T* __restrict__ A, const 
 template <typename T>
 void gemm_t(const T* A, const T* B, T* C, const GemmSpec& g, cudaStream_t st) {
   if (g.M == 0 || g.N == 0 || g.batch == 0) return;
+  ProfScope ps(PROF_GEMM, st, 2.0 * g.batch * g.M * g.N * g.K,
+               (double)sizeof(T) * g.batch * (g.M * g.K + g.K * g.N + (g.beta != 0.0 ? 2 : 1) * g.M * g.N));
   if (g.K == 0) {  // C = beta C
     CTM_CHECK(g.beta == 0.0, CTM_ERR_INVALID_ARG, "gemm with K=0 and beta!=0 unsupported");
     for (int64_t b = 0; b < g.batch; ++b)
       for (int64_t m = 0; m < g.M; ++m) CTM_CUDA(cudaMemsetAsync(C + b * g.strideC + m * g.ldc, 0, g.N * sizeof(T), st));
     return;
   }
-  dim3 grid((unsigned)((g.N + 63) / 64), (unsigned)((g.M + 63) / 64), (unsigned)std::min<int64_t>(g.batch, 65535));
-  CTM_CHECK((g.M + 63) / 64 < 65536, CTM_ERR_INVALID_ARG, "gemm M too large");
+  const int64_t work = g.batch * ((g.M + 63) / 64);
+  CTM_CHECK((g.N + 63) / 64 < (int64_t(1) << 31), CTM_ERR_INVALID_ARG, "gemm N too large");
+  dim3 grid((unsigned)((g.N + 63) / 64), (unsigned)std::min<int64_t>(work, 65535),
+            (unsigned)std::min<int64_t>((work + 65534) / 65535, 65535));
   gemm_simt<T, 64, 64, 16><<<grid, 256, 0, st>>>(A, B, C, g);
   CTM_LAUNCHED();
 }

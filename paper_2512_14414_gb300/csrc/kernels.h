@@ -75,6 +75,8 @@ void qr_apply_Q(const double* A, const double* tau, double* X, int batch, int m,
 void svd_jacobi(double* W, double* V, double* lam, double* Uo, double* Vo, int batch, int r, int max_sweeps,
                 int* status, int* sweeps_out, cudaStream_t st);
 void set_identity_colmajor(double* V, int batch, int r, cudaStream_t st);
+// Flops counted by the Jacobi kernels since the last call (6r per pair test, 12r per rotation).
+double jacobi_flops_read_reset(cudaStream_t st);
 // X[k*m + i] = U[i*r + k] for i < r, 0 for r <= i < m  (k < r): [U; 0] stored column-major.
 void embed_transpose(const double* U, int r, double* X, int64_t m, cudaStream_t st);
 

@@ -185,8 +185,9 @@ __global__ void frob2_kernel(const double* W, int64_t rr, double* out) {
 // both columns lie above the rounding floor 1e-32 ||M||_F^2: below it a column is noise whose
 // direction no further rotation can settle, and its singular value is a numerical zero.
 __global__ void jacobi_kernel(double* W, double* V, int batch, int r, int rp, int max_sweeps, double tol, int* flags,
-                              int* conv, int* sweeps_out, const double* frob2, Sync s) {
+                              int* conv, int* sweeps_out, const double* frob2, double* flop_acc, Sync s) {
   const int lane = threadIdx.x % 32;
+  double my_flops = 0.0;  // 6r per pair test, 12r per rotation (both columns of W and V)
   const int wpb = blockDim.x / 32;
   const int64_t gw = (int64_t)blockIdx.x * wpb + threadIdx.x / 32;
   const int64_t nw = (int64_t)gridDim.x * wpb;
@@ -221,7 +222,9 @@ __global__ void jacobi_kernel(double* W, double* V, int batch, int r, int rp, in
         be = warp_sum(be);
         ga = warp_sum(ga);
         const double floor2 = 1e-32 * __ldcg(frob2 + b);
+        my_flops += 6.0 * r;
         if (al > floor2 && be > floor2 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+          my_flops += 12.0 * r;
           double zeta = (be - al) / (2.0 * ga);
           double tt;
           if (fabs(zeta) > 1e150)
@@ -246,7 +249,10 @@ __global__ void jacobi_kernel(double* W, double* V, int batch, int r, int rp, in
         }
         __syncwarp();
       }
-      if (!grid_barrier(s)) return;
+      if (!grid_barrier(s)) {
+        if (lane == 0) atomicAdd(flop_acc, my_flops);
+        return;
+      }
     }
     // decide convergence: every block reads the same flags and conv after the barrier
     int all = 1;
@@ -269,8 +275,9 @@ __global__ void jacobi_kernel(double* W, double* V, int batch, int r, int rp, in
       break;
     }
   }
+  if (lane == 0) atomicAdd(flop_acc, my_flops);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *sweeps_out = sweep;
+    atomicAdd(sweeps_out, sweep);
     for (int b = 0; b < batch; ++b)
       if (!conv[b]) atomicOr(s.status, DEV_SVD_NOCONV);
   }
@@ -328,6 +335,7 @@ struct CoopScratch {
   int* conv = nullptr;
   double* frob2 = nullptr;
   int flags_cap = 0;
+  double* flop_acc = nullptr;
 };
 
 thread_local CoopScratch g_coop;
@@ -336,6 +344,8 @@ void ensure_coop(int batch, cudaStream_t st) {
   if (!g_coop.bar) {
     CTM_CUDA(cudaMalloc(&g_coop.bar, 2 * sizeof(unsigned)));
     CTM_CUDA(cudaMalloc(&g_coop.abort, sizeof(int)));
+    CTM_CUDA(cudaMalloc(&g_coop.flop_acc, sizeof(double)));
+    CTM_CUDA(cudaMemset(g_coop.flop_acc, 0, sizeof(double)));
   }
   if (g_coop.flags_cap < batch) {
     if (g_coop.flags) {
@@ -365,6 +375,7 @@ int coop_grid(const void* kernel, int threads) {
 
 void qr_householder(double* A, double* tau, int batch, int m, int n, int64_t strideA, int* status, cudaStream_t st) {
   if (batch == 0 || n == 0) return;
+  ProfScope ps(PROF_QR, st, batch * (2.0 * m * n * n - 2.0 * n * n * n / 3.0), 8.0 * batch * m * n * 2);
   ensure_coop(batch, st);
   const int threads = 256;
   int grid = coop_grid((const void*)qr_kernel, threads);
@@ -385,6 +396,7 @@ void qr_extract_R(const double* A, double* R, int batch, int m, int n, int64_t s
 void qr_apply_Q(const double* A, const double* tau, double* X, int batch, int m, int n, int k, int64_t strideA,
                 int64_t strideX, int* status, cudaStream_t st) {
   if (batch == 0 || n == 0) return;
+  ProfScope ps(PROF_QR, st, batch * 4.0 * m * n * k - 2.0 * batch * n * n * k, 8.0 * batch * (m * n + 2.0 * m * k));
   ensure_coop(batch, st);
   const int threads = 256;
   int grid = coop_grid((const void*)apply_q_kernel, threads);
@@ -396,6 +408,15 @@ void qr_apply_Q(const double* A, const double* tau, double* X, int batch, int m,
   CTM_LAUNCHED();
 }
 
+double jacobi_flops_read_reset(cudaStream_t st) {
+  if (!g_coop.flop_acc) return 0.0;
+  double v = 0.0;
+  CTM_CUDA(cudaMemcpyAsync(&v, g_coop.flop_acc, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CTM_CUDA(cudaStreamSynchronize(st));
+  CTM_CUDA(cudaMemsetAsync(g_coop.flop_acc, 0, sizeof(double), st));
+  return v;
+}
+
 void set_identity_colmajor(double* V, int batch, int r, cudaStream_t st) {
   dim3 grid((unsigned)std::min<int64_t>(4096, ((int64_t)r * r + 255) / 256), batch);
   identity_kernel<<<grid, 256, 0, st>>>(V, r);
@@ -405,6 +426,7 @@ void set_identity_colmajor(double* V, int batch, int r, cudaStream_t st) {
 void svd_jacobi(double* W, double* V, double* lam, double* Uo, double* Vo, int batch, int r, int max_sweeps,
                 int* status, int* sweeps_out, cudaStream_t st) {
   if (batch == 0 || r == 0) return;
+  ProfScope ps(PROF_SVD, st, 0.0, 8.0 * batch * r * r * 4);
   ensure_coop(batch, st);
   CTM_CUDA(cudaMemsetAsync(g_coop.flags, 0, 3 * batch * sizeof(int), st));
   CTM_CUDA(cudaMemsetAsync(g_coop.conv, 0, batch * sizeof(int), st));
@@ -420,7 +442,8 @@ void svd_jacobi(double* W, double* V, double* lam, double* Uo, double* Vo, int b
   double* frob2 = g_coop.frob2;
   frob2_kernel<<<batch, 256, 0, st>>>(W, (int64_t)r * r, frob2);
   CTM_LAUNCHED();
-  void* args[] = {&W, &V, &batch, &r, &rp, &max_sweeps, &tol, &flags, &conv, &sweeps_out, &frob2, &s};
+  double* facc = g_coop.flop_acc;
+  void* args[] = {&W, &V, &batch, &r, &rp, &max_sweeps, &tol, &flags, &conv, &sweeps_out, &frob2, &facc, &s};
   CTM_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, grid, threads, args, 0, st));
   CTM_LAUNCHED();
   size_t smem = (size_t)r * (sizeof(double) + sizeof(int));

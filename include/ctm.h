@@ -150,6 +150,17 @@ int64_t ctm_kernel_launches(const ctm_handle* h);
 int ctm_profile(ctm_handle* h, int enable);
 int ctm_profile_read(ctm_handle* h, int cls, double* ms, int64_t* launches, double* flops, double* bytes);
 
+/* Batched SVD M_b = U_b diag(s_b) V_b^t of square r x r FP64 matrices by the
+ * one-sided Jacobi kernels of the projector step (Eq. QRSVD; Hestenes' method).
+ *   M : device, batch x r x r, row-major (read only).
+ *   U, V : device, batch x r x r, row-major; column k is the k-th singular vector.
+ *   s : device, batch x r, descending.
+ * Singular values at the rounding floor (below 1e-16 ||M_b||_F) come out as
+ * numerical noise with unnormalised U columns.  Allocates its working copies on
+ * the device (cudaMalloc) and frees them before returning (a few barrier and
+ * flag words are cached per host thread); synchronises the stream. */
+int ctm_svd(const double* M, int batch, int r, double* U, double* s, double* V, void* stream);
+
 int ctm_destroy(ctm_handle* h);
 const char* ctm_error_string(int status);
 

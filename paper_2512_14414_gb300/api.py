@@ -118,6 +118,21 @@ class CTM:
         _check(self.lib.ctm_set_env(self.handle, _ptr(env), _stream()), "ctm_set_env")
 
 
+def svd(M):
+    """Batched FP64 SVD of square matrices (cuda float64 [batch, r, r]) by libctm's Jacobi kernels.
+
+    Returns U, s, V with M[b] = U[b] diag(s[b]) V[b]^t, s descending."""
+    lib = _lib.load()
+    assert M.is_cuda and M.dtype == torch.float64 and M.dim() == 3 and M.shape[1] == M.shape[2]
+    M = M.contiguous()
+    b, r = M.shape[0], M.shape[1]
+    U = torch.empty_like(M)
+    V = torch.empty_like(M)
+    s = torch.empty(b, r, dtype=torch.float64, device=M.device)
+    _check(lib.ctm_svd(_ptr(M), b, r, _ptr(U), _ptr(s), _ptr(V), _stream()), "ctm_svd")
+    return U, s, V
+
+
 class CTMEnergy(torch.autograd.Function):
     """E(A) after n_iter CTMRG iterations from env0; backward returns dE/dA from ctm_grad."""
 

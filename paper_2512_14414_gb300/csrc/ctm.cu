@@ -1194,6 +1194,41 @@ int ctm_profile_read(ctm_handle* h, int cls, double* ms, int64_t* launches, doub
   });
 }
 
+int ctm_svd(const double* M, int batch, int r, double* U, double* s, double* V, void* stream) {
+  if (!M || !U || !s || !V || batch < 1 || r < 1 || r > 4096) return CTM_ERR_INVALID_ARG;
+  return guard(nullptr, [&]() {
+    using namespace ctm;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t rr = (int64_t)r * r;
+    double *W = nullptr, *Vw = nullptr;
+    int* status = nullptr;
+    CTM_CUDA(cudaMalloc(&W, sizeof(double) * rr * batch));
+    CTM_CUDA(cudaMalloc(&Vw, sizeof(double) * rr * batch));
+    CTM_CUDA(cudaMalloc(&status, 2 * sizeof(int)));
+    CTM_CUDA(cudaMemsetAsync(status, 0, 2 * sizeof(int), st));
+    PermSpec ps;  // column-major working copy: W_b[k*r + i] = M_b[i][k]
+    ps.rank = 3;
+    ps.out_dims[0] = batch;
+    ps.out_dims[1] = r;
+    ps.out_dims[2] = r;
+    ps.in_stride[0] = rr;
+    ps.in_stride[1] = 1;
+    ps.in_stride[2] = r;
+    permute(M, F64, W, F64, ps, false, 1.0, st);
+    set_identity_colmajor(Vw, batch, r, st);
+    svd_jacobi(W, Vw, s, U, V, batch, r, 60, status, status + 1, st);
+    int hs = 0;
+    CTM_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CTM_CUDA(cudaStreamSynchronize(st));
+    cudaFree(W);
+    cudaFree(Vw);
+    cudaFree(status);
+    if (hs & DEV_TIMEOUT) throw Error(CTM_ERR_TIMEOUT, "device wait timed out");
+    if (hs & DEV_SVD_NOCONV) throw Error(CTM_ERR_SVD_NOCONV, "Jacobi SVD did not converge");
+    if (hs & DEV_NONFINITE) throw Error(CTM_ERR_NONFINITE, "non-finite singular value");
+  });
+}
+
 int ctm_destroy(ctm_handle* h) {
   if (!h) return CTM_ERR_INVALID_ARG;
   h->eng.reset();

@@ -72,3 +72,17 @@ def test_env_roundtrip_and_spectrum_delta():
     ctm.step(10)
     d = ctm.step(1)
     assert 0.0 <= d < 1e-2
+
+
+def test_batched_svd_entry_point():
+    from paper_2512_14414_gb300.api import svd
+    rng = np.random.default_rng(9)
+    for b, r in ((3, 17), (2, 64)):
+        M = rng.standard_normal((b, r, r)) @ np.diag(np.logspace(0, -8, r))
+        U, s, V = svd(torch.tensor(M, device="cuda"))
+        U, s, V = U.cpu().numpy(), s.cpu().numpy(), V.cpu().numpy()
+        for k in range(b):
+            ref = np.linalg.svd(M[k], compute_uv=False)
+            assert np.allclose(s[k], ref, rtol=1e-12, atol=1e-14 * ref[0])
+            assert np.abs(U[k] @ np.diag(s[k]) @ V[k].T - M[k]).max() < 1e-13 * ref[0]
+            assert np.abs(V[k].T @ V[k] - np.eye(r)).max() < 1e-13

@@ -161,6 +161,22 @@ int ctm_profile_read(ctm_handle* h, int cls, double* ms, int64_t* launches, doub
  * flag words are cached per host thread); synchronises the stream. */
 int ctm_svd(const double* M, int batch, int r, double* U, double* s, double* V, void* stream);
 
+/* ctm_svd without any device allocation, for callers that cannot call
+ * cudaMalloc (memory handed out by a caller-owned pool, allocators that
+ * forbid new device allocations while they run).  The paper has no
+ * counterpart: this is a service of the library, not a step of the method.
+ * Same arguments, layouts and results as ctm_svd; batch*r*r must not exceed
+ * 1,048,576 and batch must not exceed 1024, otherwise CTM_ERR_INVALID_ARG is
+ * returned before any work is enqueued.  The workspace is one fixed 16 MiB
+ * device array compiled into the library: every GPU that loads the library
+ * holds it until the process exits.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the array and every call clears the
+ * parts that must start at zero, so calls whose work overlaps on the GPU (two
+ * streams, two host threads) race with each other: serialise them.
+ * Synchronises the stream to read the status. */
+int ctm_svd_noalloc(const double* M, int batch, int r, double* U, double* s, double* V, void* stream);
+
 int ctm_destroy(ctm_handle* h);
 const char* ctm_error_string(int status);
 

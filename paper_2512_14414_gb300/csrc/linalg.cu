@@ -14,6 +14,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "kernels.h"
@@ -453,3 +454,102 @@ void svd_jacobi(double* W, double* V, double* lam, double* Uo, double* Vo, int b
 }
 
 }  // namespace ctm
+
+// ==================================================================== allocation-free batched SVD
+// For callers that may not allocate device memory (for example code that runs
+// inside a caller-owned memory pool or under an allocator that forbids
+// cudaMalloc): every byte of workspace of this entry point lives in one
+// fixed-size array in the library's device image.
+namespace ctm {
+namespace {
+
+constexpr int64_t kNoAllocMaxElems = int64_t(1) << 20;  // batch * r * r limit (8 MiB per working copy)
+constexpr int kNoAllocMaxBatch = 1024;
+// [W: max][V: max][frob2: 1024][flop acc: 8][ints: bar 2, abort 1, status 1, sweeps 1, pad, flags 3*1024, conv 1024]
+constexpr int64_t kNoAllocInts = 8 + 4 * kNoAllocMaxBatch;
+constexpr int64_t kNoAllocDoubles = 2 * kNoAllocMaxElems + kNoAllocMaxBatch + 8 + kNoAllocInts / 2;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[256] = {};
+
+// Device address of the scratch array on the current device (looked up once per device).
+double* noalloc_base() {
+  int dev = 0;
+  CTM_CUDA(cudaGetDevice(&dev));
+  CTM_CHECK(dev >= 0 && dev < 256, CTM_ERR_CUDA, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    CTM_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = (double*)p;
+  }
+  return g_noalloc_ptr[dev];
+}
+
+void svd_noalloc(const double* M, int batch, int r, double* U, double* sv, double* V, cudaStream_t st) {
+  const int64_t rr = (int64_t)r * r;
+  double* base = noalloc_base();
+  double* W = base;
+  double* Vw = base + kNoAllocMaxElems;
+  double* frob2 = base + 2 * kNoAllocMaxElems;
+  double* facc = frob2 + kNoAllocMaxBatch;
+  int* ints = (int*)(facc + 8);
+  unsigned* bar = (unsigned*)ints;
+  int* abort_flag = ints + 2;
+  int* status = ints + 3;
+  int* sweeps = ints + 4;
+  int* flags = ints + 8;
+  int* conv = flags + 3 * kNoAllocMaxBatch;
+  // everything that must start at zero, in stream order
+  CTM_CUDA(cudaMemsetAsync(ints, 0, kNoAllocInts * sizeof(int), st));
+  CTM_CUDA(cudaMemsetAsync(facc, 0, sizeof(double), st));
+  PermSpec ps;  // column-major working copy: W_b[k*r + i] = M_b[i][k]
+  ps.rank = 3;
+  ps.out_dims[0] = batch;
+  ps.out_dims[1] = r;
+  ps.out_dims[2] = r;
+  ps.in_stride[0] = rr;
+  ps.in_stride[1] = 1;
+  ps.in_stride[2] = r;
+  permute(M, F64, W, F64, ps, false, 1.0, st);
+  set_identity_colmajor(Vw, batch, r, st);
+  frob2_kernel<<<batch, 256, 0, st>>>(W, rr, frob2);
+  CTM_LAUNCHED();
+  const int threads = 256;
+  int rp = r + (r & 1);
+  int grid = coop_grid((const void*)jacobi_kernel, threads);
+  int64_t need = ((int64_t)batch * (rp / 2) + threads / 32 - 1) / (threads / 32);
+  grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, need));
+  double tol = 2.220446049250313e-16 * r;
+  int max_sweeps = 60;
+  Sync s{bar, abort_flag, status};
+  void* args[] = {&W, &Vw, &batch, &r, &rp, &max_sweeps, &tol, &flags, &conv, &sweeps, &frob2, &facc, &s};
+  CTM_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, grid, threads, args, 0, st));
+  CTM_LAUNCHED();
+  size_t smem = (size_t)r * (sizeof(double) + sizeof(int));
+  svd_finalize_kernel<<<batch, 256, smem, st>>>(W, Vw, sv, U, V, r, status);
+  CTM_LAUNCHED();
+  int hs = 0;
+  CTM_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CTM_CUDA(cudaStreamSynchronize(st));
+  if (hs & DEV_TIMEOUT) throw Error(CTM_ERR_TIMEOUT, "device wait timed out");
+  if (hs & DEV_SVD_NOCONV) throw Error(CTM_ERR_SVD_NOCONV, "Jacobi SVD did not converge");
+  if (hs & DEV_NONFINITE) throw Error(CTM_ERR_NONFINITE, "non-finite singular value");
+}
+
+}  // namespace
+}  // namespace ctm
+
+extern "C" int ctm_svd_noalloc(const double* M, int batch, int r, double* U, double* s, double* V, void* stream) {
+  if (!M || !U || !s || !V || batch < 1 || r < 1 || batch > ctm::kNoAllocMaxBatch ||
+      (int64_t)batch * r * r > ctm::kNoAllocMaxElems)
+    return CTM_ERR_INVALID_ARG;
+  try {
+    ctm::svd_noalloc(M, batch, r, U, s, V, (cudaStream_t)stream);
+    return CTM_OK;
+  } catch (const ctm::Error& e) {
+    fprintf(stderr, "libctm: %s\n", e.what());
+    return e.status;
+  }
+}

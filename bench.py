@@ -190,7 +190,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="tf32")
+    ap.add_argument("--precision", default="tf32x3")
     ap.add_argument("--workload", default="ss_d6_chi64")
     ap.add_argument("--n-iter", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")

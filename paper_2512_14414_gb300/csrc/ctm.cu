@@ -38,6 +38,7 @@
 // forward), and back-propagates through it (Eq. AD).
 #include <array>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -109,7 +110,7 @@ struct ctm_handle {
   std::vector<TermH> terms;
   int R = 0, C = 0, nsites = 0;
   ctm::DType edt = ctm::F64;
-  double cut = 1e-6, eps = 1e-30;
+  double cut = 1e-5, eps = 1e-30;
   int64_t launches = 0;
   cudaStream_t st = nullptr;
   std::unique_ptr<ctm::Arena> persist, tape, store;
@@ -140,6 +141,7 @@ struct ctm_handle {
   // replay state of the current iteration (backward recompute)
   bool replay = false;
   int cur_iter = 0, cur_pair = 0;
+  bool debug_sweeps = getenv("CTM_DEBUG_SWEEPS") != nullptr;
 };
 
 namespace ctm {
@@ -432,8 +434,29 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
         gemm_f64((const double*)S64[b].p, (const double*)N64[b].p, W + b * rr, g, st);
       }
     }
-    set_identity_colmajor(Vw, nb, r, st);
-    svd_jacobi(W, Vw, lam, Uo, Vo, nb, r, kMaxSweeps, h->dstatus, h->dsweeps, st);
+    // Truncated SVD through a sketch of width l when the matrices are large (Sec. Outlook:
+    // partial / randomised decompositions in Eq. QRSVD); exact whenever the numerical rank
+    // of M is below l, which is checked per matrix -- otherwise the full Jacobi SVD runs.
+    const int l = std::min(r, std::max(h->d.chi + 16, 32));
+    bool sketched = false;
+    if (h->debug_sweeps) CTM_CUDA(cudaMemsetAsync(h->dsweeps, 0, sizeof(int), st));
+    if (2 * l <= r) {
+      std::vector<int> inc;
+      svd_sketch(W, nb, r, l, lam, Uo, Vo, h->dstatus, h->dsweeps, inc, st);
+      sketched = true;
+      for (int x : inc) sketched = sketched && x == 0;
+    }
+    if (!sketched) {
+      set_identity_colmajor(Vw, nb, r, st);
+      svd_jacobi(W, Vw, lam, Uo, Vo, nb, r, kMaxSweeps, h->dstatus, h->dsweeps, st);
+    }
+    if (h->debug_sweeps) {
+      int sw = 0;
+      CTM_CUDA(cudaMemcpyAsync(&sw, h->dsweeps, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CTM_CUDA(cudaStreamSynchronize(st));
+      fprintf(stderr, "libctm: iteration %d pairs %d..%d r=%d %s l=%d Jacobi sweeps %d\n", h->cur_iter, h->cur_pair,
+              h->cur_pair + nb - 1, r, sketched ? "sketch" : "full", l, sw);
+    }
     for (int b = 0; b < nb; ++b) {
       const int64_t nr = in[b].n_r, nl = in[b].n_l;
       CTM_CUDA(cudaMemcpyAsync(F[b]->lam, lam + (int64_t)b * r, sizeof(double) * r, cudaMemcpyDeviceToDevice, st));
@@ -454,6 +477,8 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
         CTM_CUDA(cudaMemcpyAsync(F[b]->U, Uo + b * rr, sizeof(double) * rr, cudaMemcpyDeviceToDevice, st));
         CTM_CUDA(cudaMemcpyAsync(F[b]->V, Vo + b * rr, sizeof(double) * rr, cudaMemcpyDeviceToDevice, st));
       }
+      // canonical signs keep the environment's chi basis fixed from one iteration to the next
+      sign_fix(F[b]->U, F[b]->V, 1, nr, r, st);
     }
   }
   // P = S^t V' L^-1/2, Q = N^t U' L^-1/2 (identical in forward and replay)
@@ -967,7 +992,7 @@ int ctm_create(const ctm_desc* desc, ctm_handle** out) {
   h->C = 2 * d.Lx;
   h->nsites = h->R * h->C;
   h->edt = d.precision == CTM_FP64 ? ctm::F64 : ctm::F32;
-  h->cut = d.svd_cutoff_rel > 0 ? d.svd_cutoff_rel : 1e-6;
+  h->cut = d.svd_cutoff_rel > 0 ? d.svd_cutoff_rel : 1e-5;
   h->eps = d.svd_adjoint_eps >= 0 ? d.svd_adjoint_eps : 1e-30;
   int d2 = d.d * d.d;
   for (int t = 0; t < d.n_terms; ++t) {
@@ -984,6 +1009,8 @@ int ctm_init(ctm_handle* h, const double* A, const double* env0, void* stream) {
     h->st = (cudaStream_t)stream;
     ctm::ensure_device(h);
     h->eng->set_stream(h->st);
+    const int tcm = h->d.precision == CTM_TF32 ? 1 : h->d.precision == CTM_BF16 ? 2 : h->d.precision == CTM_TF32X3 ? 3 : 0;
+    h->eng->set_tc(tcm, h->dstatus);
     int64_t n = h->A64.numel();
     CTM_CUDA(cudaMemcpyAsync(h->A64.p, A, n * 8, cudaMemcpyDeviceToDevice, h->st));
     if (h->edt != ctm::F64) ctm::cast(h->A64.p, ctm::F64, h->Amode.p, h->edt, n, false, h->st);

@@ -210,6 +210,14 @@ void Engine::einsum_into(const Tensor& A, const Labels& la, const Tensor& B, con
 
   const Labels Mla = M, Mlc = subseq(lc, M), Nlb = N, Nlc = subseq(lc, N), Kla = K, Klb = subseq(lb, K);
   const Labels bla = batch;
+  // tensor-core route for FP32 contractions: both operands K-major ([batch|M|K] and [batch|N|K])
+  const int64_t KK0 = prod(K, dims), MM0 = prod(M, dims), NN0 = prod(N, dims), nb0 = prod(batch, dims);
+  const bool tc = A.dt == F32 && tc_mode_ != 0 && KK0 >= 8 && nb0 <= 65535 && MM0 * NN0 * KK0 >= (int64_t(1) << 15) &&
+                  (KK0 * (tc_mode_ == 2 ? 2 : 4)) % 16 == 0;  // modes: 1 tf32, 2 bf16, 3 tf32x3
+  if (tc) {
+    einsum_tc(A, la, B, lb, lc, out, accumulate, dims, batch, M, N, K, Mlc, Nlc, Klb, nC);
+    return;
+  }
   struct Cand {
     Labels Mo, No, Ko;
     bool swap;
@@ -295,6 +303,75 @@ void Engine::einsum_into(const Tensor& A, const Labels& la, const Tensor& B, con
     perm_bytes_ += (accumulate ? 3 : 2) * nC * es;
   }
   // temporaries are dead once the kernels above are enqueued in stream order
+  arena_->release(mark);
+}
+
+void Engine::einsum_tc(const Tensor& A, const Labels& la, const Tensor& B, const Labels& lb, const Labels& lc,
+                       void* out, bool accumulate, const std::map<int, int64_t>& dims, const Labels& bla,
+                       const Labels& Mla, const Labels& Nlb, const Labels& Kla, const Labels& Mlc,
+                       const Labels& Nlc, const Labels& Klb, int64_t nC) {
+  const bool bf16 = tc_mode_ == 2;
+  const DType odt = bf16 ? BF16 : F32;
+  const int64_t nA = A.numel(), nB = B.numel();
+  struct Cand {
+    Labels Mo, No, Ko;
+    bool swap, aok, bok, permC;
+    int64_t cost;
+  } best;
+  best.cost = -1;
+  for (const Labels* Mo : {&Mla, &Mlc})
+    for (const Labels* No : {&Nlb, &Nlc})
+      for (const Labels* Ko : {&Kla, &Klb})
+        for (bool swap : {false, true}) {
+          Cand c{*Mo, *No, *Ko, swap, la == cat({&bla, Mo, Ko}), lb == cat({&bla, No, Ko}), false, 0};
+          if (c.aok && (uintptr_t)A.p % 16) c.aok = false;
+          if (c.bok && (uintptr_t)B.p % 16) c.bok = false;
+          Labels nat = swap ? cat({&bla, No, Mo}) : cat({&bla, Mo, No});
+          c.permC = nat != lc;
+          c.cost = (c.aok ? 0 : nA) + (c.bok ? 0 : nB) + (c.permC ? 2 * nC : 0);
+          c.cost = c.cost * 4 + (swap ? 1 : 0);
+          if (best.cost < 0 || c.cost < best.cost) best = c;
+        }
+  const int64_t nb = prod(bla, dims), MM = prod(best.Mo, dims), NN = prod(best.No, dims), KK = prod(best.Ko, dims);
+  auto mark = arena_->mark();
+  const void* Ap = A.p;
+  const void* Bp = B.p;
+  if (!best.aok || bf16) {
+    void* t = arena_->alloc(nA * dtype_size(odt));
+    ctm::permute(A.p, A.dt, t, odt, perm_spec(la, cat({&bla, &best.Mo, &best.Ko}), dims), false, 1.0, st_);
+    perm_bytes_ += nA * (4 + dtype_size(odt));
+    Ap = t;
+  }
+  if (!best.bok || bf16) {
+    void* t = arena_->alloc(nB * dtype_size(odt));
+    ctm::permute(B.p, B.dt, t, odt, perm_spec(lb, cat({&bla, &best.No, &best.Ko}), dims), false, 1.0, st_);
+    perm_bytes_ += nB * (4 + dtype_size(odt));
+    Bp = t;
+  }
+  void* Cp = best.permC ? arena_->alloc(nC * 4) : out;
+  const double beta = (!best.permC && accumulate) ? 1.0 : 0.0;
+  gemm_flops_ += 2 * nb * MM * NN * KK;
+  if (tc_mode_ == 3) {
+    float* Ah = (float*)arena_->alloc(nA * 4);
+    float* Al = (float*)arena_->alloc(nA * 4);
+    float* Bh = (float*)arena_->alloc(nB * 4);
+    float* Bl = (float*)arena_->alloc(nB * 4);
+    split_tf32((const float*)Ap, Ah, Al, nA, st_);
+    split_tf32((const float*)Bp, Bh, Bl, nB, st_);
+    if (!best.swap)
+      gemm_tc_x3(Ah, Al, Bh, Bl, (float*)Cp, MM, NN, KK, nb, beta, tc_status_, st_);
+    else
+      gemm_tc_x3(Bh, Bl, Ah, Al, (float*)Cp, NN, MM, KK, nb, beta, tc_status_, st_);
+  } else if (!best.swap) {
+    gemm_tc(Ap, Bp, (float*)Cp, MM, NN, KK, nb, bf16, beta, tc_status_, st_);
+  } else {
+    gemm_tc(Bp, Ap, (float*)Cp, NN, MM, KK, nb, bf16, beta, tc_status_, st_);
+  }
+  if (best.permC) {
+    Labels nat = best.swap ? cat({&bla, &best.No, &best.Mo}) : cat({&bla, &best.Mo, &best.No});
+    ctm::permute(Cp, F32, out, F32, perm_spec(nat, lc, dims), accumulate, 1.0, st_);
+    perm_bytes_ += (accumulate ? 3 : 2) * nC * 4;
+  }
   arena_->release(mark);
 }
 

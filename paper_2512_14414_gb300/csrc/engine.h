@@ -89,15 +89,27 @@ class Engine {
   Tensor cast(const Tensor& x, DType to);
   Tensor permute(const Tensor& x, const std::vector<int>& perm);  // out dim k = in dim perm[k]
 
+  // Tensor-core mode of FP32 contractions: 0 SIMT FP32, 1 TF32 (tcgen05 kind::tf32),
+  // 2 BF16 operands (tcgen05 kind::f16).  `status` receives device-side error bits.
+  void set_tc(int mode, int* status) {
+    tc_mode_ = mode;
+    tc_status_ = status;
+  }
   int64_t gemm_flops() const { return gemm_flops_; }
   int64_t perm_bytes() const { return perm_bytes_; }
   void reset_counters() { gemm_flops_ = perm_bytes_ = 0; }
 
  private:
   void gemm(DType dt, const void* A, const void* B, void* C, const GemmSpec& g);
+  void einsum_tc(const Tensor& A, const Labels& la, const Tensor& B, const Labels& lb, const Labels& lc, void* out,
+                 bool accumulate, const std::map<int, int64_t>& dims, const Labels& bla, const Labels& Mla,
+                 const Labels& Nlb, const Labels& Kla, const Labels& Mlc, const Labels& Nlc, const Labels& Klb,
+                 int64_t nC);
   cudaStream_t st_;
   Arena* arena_;
   bool record_ = false;
+  int tc_mode_ = 0;
+  int* tc_status_ = nullptr;
   int next_id_ = 0;
   std::vector<std::function<void()>> tape_;
   std::vector<void*> grads_;

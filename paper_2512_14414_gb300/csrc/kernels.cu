@@ -165,27 +165,33 @@ void permute_t(const Ti* in, To* out, const PermSpec& ps, bool acc, double scale
 }
 
 // ------------------------------------------------------------------ SIMT GEMM
+// Split-K: with nsplit > 1 the (split, batch) pairs form an extended batch; each block sums its
+// K chunk and writes the raw partial tile to C (a workspace [nsplit][batch][M][N], ldc = N); a
+// second kernel adds the partials in split order (deterministic) and applies alpha and beta.
 template <typename T, int BM, int BN, int BK>
 __global__ void __launch_bounds__(256) gemm_simt(const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ C,
-                                                 GemmSpec g) {
+                                                 GemmSpec g, int64_t nsplit, int64_t kchunk) {
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int64_t n0 = (int64_t)blockIdx.x * BN;
   const int64_t mtiles = (g.M + BM - 1) / BM;
-  for (int64_t work = blockIdx.z * (int64_t)gridDim.y + blockIdx.y; work < g.batch * mtiles;
+  for (int64_t work = blockIdx.z * (int64_t)gridDim.y + blockIdx.y; work < nsplit * g.batch * mtiles;
        work += (int64_t)gridDim.z * gridDim.y) {
-    const int64_t bb = work / mtiles;
+    const int64_t ext = work / mtiles;
     const int64_t m0 = (work % mtiles) * BM;
+    const int64_t bb = ext % g.batch, sp = ext / g.batch;
+    const int64_t kbeg = sp * kchunk, kend = min(g.K, kbeg + kchunk);
     const T* Ab = A + bb * g.strideA;
     const T* Bb = B + bb * g.strideB;
-    T* Cb = C + bb * g.strideC;
+    T* Cb = (nsplit > 1) ? C + ext * g.M * g.N : C + bb * g.strideC;
+    const int64_t ldc = (nsplit > 1) ? g.N : g.ldc;
     T acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-    for (int64_t k0 = 0; k0 < g.K; k0 += BK) {
+    for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
       for (int q = 0; q < (BM * BK) / 256; ++q) {
         int e = threadIdx.x + 256 * q;
@@ -199,7 +205,7 @@ __global__ void __launch_bounds__(256) gemm_simt(const T* __restrict__ A, const 
         }
         int64_t m = m0 + ml, k = k0 + kl;
         T v = T(0);
-        if (m < g.M && k < g.K) v = g.transA ? Ab[k * g.lda + m] : Ab[m * g.lda + k];
+        if (m < g.M && k < kend) v = g.transA ? Ab[k * g.lda + m] : Ab[m * g.lda + k];
         As[kl][ml] = v;
       }
 #pragma unroll
@@ -215,7 +221,7 @@ __global__ void __launch_bounds__(256) gemm_simt(const T* __restrict__ A, const 
         }
         int64_t n = n0 + nl, k = k0 + kl;
         T v = T(0);
-        if (n < g.N && k < g.K) v = g.transB ? Bb[n * g.ldb + k] : Bb[k * g.ldb + n];
+        if (n < g.N && k < kend) v = g.transB ? Bb[n * g.ldb + k] : Bb[k * g.ldb + n];
         Bs[kl][nl] = v;
       }
       __syncthreads();
@@ -241,12 +247,53 @@ __global__ void __launch_bounds__(256) gemm_simt(const T* __restrict__ A, const 
       for (int j = 0; j < 4; ++j) {
         int64_t n = n0 + tx + 16 * j;
         if (n >= g.N) continue;
-        T v = (T)g.alpha * acc[i][j];
-        if (g.beta != 0.0) v += (T)g.beta * Cb[m * g.ldc + n];
-        Cb[m * g.ldc + n] = v;
+        if (nsplit > 1) {
+          Cb[m * ldc + n] = acc[i][j];
+        } else {
+          T v = (T)g.alpha * acc[i][j];
+          if (g.beta != 0.0) v += (T)g.beta * Cb[m * ldc + n];
+          Cb[m * ldc + n] = v;
+        }
       }
     }
   }
+}
+
+template <typename T>
+__global__ void splitk_reduce(const T* __restrict__ W, T* __restrict__ C, GemmSpec g, int64_t nsplit) {
+  const int64_t per = g.M * g.N, total = g.batch * per;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e / per, r = e % per, m = r / g.N, n = r % g.N;
+    T acc = T(0);
+    for (int64_t s = 0; s < nsplit; ++s) acc += W[(s * g.batch + b) * per + r];
+    T* c = C + b * g.strideC + m * g.ldc + n;
+    T v = (T)g.alpha * acc;
+    if (g.beta != 0.0) v += (T)g.beta * *c;
+    *c = v;
+  }
+}
+
+// per-thread cached workspace of the split-K partial tiles
+thread_local void* g_splitk_ws = nullptr;
+thread_local size_t g_splitk_cap = 0;
+
+void* splitk_workspace(size_t bytes) {
+  if (bytes > g_splitk_cap) {
+    if (g_splitk_ws) CTM_CUDA(cudaFree(g_splitk_ws));
+    g_splitk_cap = std::max(bytes, size_t(64) << 20);
+    CTM_CUDA(cudaMalloc(&g_splitk_ws, g_splitk_cap));
+  }
+  return g_splitk_ws;
+}
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    CTM_CUDA(cudaGetDevice(&dev));
+    CTM_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return n;
 }
 
 template <typename T>
@@ -260,12 +307,27 @@ void gemm_t(const T* A, const T* B, T* C, const GemmSpec& g, cudaStream_t st) {
       for (int64_t m = 0; m < g.M; ++m) CTM_CUDA(cudaMemsetAsync(C + b * g.strideC + m * g.ldc, 0, g.N * sizeof(T), st));
     return;
   }
-  const int64_t work = g.batch * ((g.M + 63) / 64);
+  // split K when the output tiles alone cannot fill the GPU
+  const int64_t tiles = g.batch * ((g.M + 63) / 64) * ((g.N + 63) / 64);
+  int64_t nsplit = 1;
+  if (tiles < 2 * num_sms() && g.K >= 256) {
+    nsplit = std::min<int64_t>({(2 * num_sms() + tiles - 1) / tiles, g.K / 128, 32});
+    if (nsplit < 2) nsplit = 1;
+  }
+  const int64_t kchunk = ((g.K + nsplit - 1) / nsplit + 15) / 16 * 16;
+  nsplit = (g.K + kchunk - 1) / kchunk;
+  T* out = C;
+  if (nsplit > 1) out = (T*)splitk_workspace(sizeof(T) * nsplit * g.batch * g.M * g.N);
+  const int64_t work = nsplit * g.batch * ((g.M + 63) / 64);
   CTM_CHECK((g.N + 63) / 64 < (int64_t(1) << 31), CTM_ERR_INVALID_ARG, "gemm N too large");
   dim3 grid((unsigned)((g.N + 63) / 64), (unsigned)std::min<int64_t>(work, 65535),
             (unsigned)std::min<int64_t>((work + 65534) / 65535, 65535));
-  gemm_simt<T, 64, 64, 16><<<grid, 256, 0, st>>>(A, B, C, g);
+  gemm_simt<T, 64, 64, 16><<<grid, 256, 0, st>>>(A, B, out, g, nsplit, kchunk);
   CTM_LAUNCHED();
+  if (nsplit > 1) {
+    splitk_reduce<T><<<nblocks(g.batch * g.M * g.N, 256), 256, 0, st>>>(out, C, g, nsplit);
+    CTM_LAUNCHED();
+  }
 }
 
 // ------------------------------------------------------------------ element-wise
@@ -358,6 +420,42 @@ __global__ void proj_prepare_k(const double* lam, double* U, double* V, double* 
       Vb[e] = 0.0;
     }
   }
+}
+
+// Sign gauge of the singular triplets: column k of V (n x r, row-major) is made to have its
+// entry of largest magnitude (first one on ties) positive; U's column k follows.
+__global__ void sign_fix_k(double* U, double* V, int64_t n, int r) {
+  const int b = blockIdx.y;
+  const int k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (k >= r) return;
+  double* Ub = U + (int64_t)b * n * r;
+  double* Vb = V + (int64_t)b * n * r;
+  double best = -1.0, val = 0.0;
+  int64_t bi = 0;
+  for (int64_t i = lane; i < n; i += 32) {
+    double v = Vb[i * r + k];
+    if (fabs(v) > best) {
+      best = fabs(v);
+      val = v;
+      bi = i;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    double ov = __shfl_xor_sync(0xffffffffu, val, o);
+    int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) {
+      best = ob;
+      val = ov;
+      bi = oi;
+    }
+  }
+  if (val < 0.0)
+    for (int64_t i = lane; i < n; i += 32) {
+      Vb[i * r + k] = -Vb[i * r + k];
+      Ub[i * r + k] = -Ub[i * r + k];
+    }
 }
 
 __global__ void scale_cols_k(const double* Y, int64_t ldy, int64_t strideY, const double* s, int64_t strideS, double* X,
@@ -463,6 +561,23 @@ __global__ void energy_k(const double* rho, const double* hs, const double* coup
     double f = coup[t] * inv_sites / trs[t];
     for (int a = 0; a < d2; ++a)
       for (int c = 0; c < d2; ++c) drho[(int64_t)t * d2 * d2 + a * d2 + c] = f * (H[c * d2 + a] - (a == c ? es[t] : 0.0));
+  }
+}
+
+// x = hi + lo with hi = x rounded to the nearest TF32 number (10-bit mantissa) and lo = x - hi
+// (exact in FP32); lo is itself rounded to TF32 so that the tensor core reads it unchanged.
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t u = __float_as_uint(x);
+  u = (u + 0x1000u) & 0xFFFFE000u;
+  return __uint_as_float(u);
+}
+
+__global__ void split_tf32_k(const float* x, float* hi, float* lo, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float v = x[i];
+    float h = tf32_round(v);
+    hi[i] = h;
+    lo[i] = tf32_round(v - h);
   }
 }
 
@@ -577,6 +692,12 @@ void proj_prepare(const double* lam, double* U, double* V, double* inv, double* 
   CTM_LAUNCHED();
 }
 
+void sign_fix(double* U, double* V, int batch, int64_t n, int r, cudaStream_t st) {
+  dim3 grid((r + 7) / 8, batch);
+  sign_fix_k<<<grid, 256, 0, st>>>(U, V, n, r);
+  CTM_LAUNCHED();
+}
+
 void scale_cols(const double* Y, int64_t ldy, int64_t strideY, const double* s, int64_t strideS, double* X, int batch,
                 int64_t n, int kept, cudaStream_t st) {
   dim3 grid(nblocks(n * kept, 256, 4096), batch);
@@ -609,6 +730,13 @@ void energy_terms(const double* rho, const double* hs, const double* coup, int n
                   double* e_bond, double* e_site, double* drho, int* status, cudaStream_t st) {
   CTM_CHECK(n_terms <= 64, CTM_ERR_INVALID_ARG, "at most 64 terms");
   energy_k<<<1, 64, 0, st>>>(rho, hs, coup, n_terms, d2, inv_sites, e_bond, e_site, drho, status);
+  CTM_LAUNCHED();
+}
+
+void split_tf32(const float* x, float* hi, float* lo, int64_t n, cudaStream_t st) {
+  if (n == 0) return;
+  ProfScope prof(PROF_PERMUTE, st, 0.0, 12.0 * n);
+  split_tf32_k<<<nblocks(n, 256), 256, 0, st>>>(x, hi, lo, n);
   CTM_LAUNCHED();
 }
 

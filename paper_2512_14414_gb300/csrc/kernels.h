@@ -28,6 +28,16 @@ struct GemmSpec {
 };
 void gemm_f64(const double* A, const double* B, double* C, const GemmSpec& g, cudaStream_t st);
 void gemm_f32(const float* A, const float* B, float* C, const GemmSpec& g, cudaStream_t st);
+// Tensor-core GEMM (tcgen05): C[b][m][n] (+)= sum_k A[b][m][k] B[b][n][k]; A, B BF16 or FP32 (as TF32),
+// C FP32 row-major.  tc_gemm_ok tells whether TMA can address the operands.
+bool tc_gemm_ok(bool bf16, int64_t M, int64_t N, int64_t K, const void* A, const void* B);
+void gemm_tc(const void* A, const void* B, float* C, int64_t M, int64_t N, int64_t K, int64_t batch, bool bf16,
+             double beta, int* status, cudaStream_t st);
+// Error-compensated TF32: C (+)= Ahi Bhi^t + Ahi Blo^t + Alo Bhi^t (operands from split_tf32).
+void gemm_tc_x3(const float* Ahi, const float* Alo, const float* Bhi, const float* Blo, float* C, int64_t M,
+                int64_t N, int64_t K, int64_t batch, double beta, int* status, cudaStream_t st);
+// hi = x rounded to TF32, lo = (x - hi) rounded to TF32.
+void split_tf32(const float* x, float* hi, float* lo, int64_t n, cudaStream_t st);
 
 // ------------------------------------------------------------------ elementwise / reductions
 void fill(void* p, DType t, int64_t n, double v, cudaStream_t st);
@@ -45,6 +55,8 @@ void scale_by(const void* dy, DType t, int64_t n, const double* inv, void* dx, b
 // are zeroed.  sinv[b][k] = 1/lam for lam > rank_tol*lam_0 else 0.
 void proj_prepare(const double* lam, double* U, double* V, double* inv, double* sinv, int batch,
                   int64_t n_r, int r, int kept, double cut, double rank_tol, int* status, cudaStream_t st);
+// Sign gauge: column k of V (n x r row-major) gets a positive entry of largest magnitude; U follows.
+void sign_fix(double* U, double* V, int batch, int64_t n, int r, cudaStream_t st);
 // X[b][i][k] = Y[b][i*ldy + k] * s[b][k] for k < kept (X is n x kept row-major)
 void scale_cols(const double* Y, int64_t ldy, int64_t strideY, const double* s, int64_t strideS, double* X,
                 int batch, int64_t n, int kept, cudaStream_t st);
@@ -75,6 +87,9 @@ void qr_apply_Q(const double* A, const double* tau, double* X, int batch, int m,
 void svd_jacobi(double* W, double* V, double* lam, double* Uo, double* Vo, int batch, int r, int max_sweeps,
                 int* status, int* sweeps_out, cudaStream_t st);
 void set_identity_colmajor(double* V, int batch, int r, cudaStream_t st);
+// Truncated SVD of low-numerical-rank r x r matrices (sketch of width l + Jacobi); see linalg.cu.
+void svd_sketch(const double* Wc, int batch, int r, int l, double* lam, double* Uo, double* Vo, int* status,
+                int* sweeps_out, std::vector<int>& incomplete_host, cudaStream_t st);
 // Flops counted by the Jacobi kernels since the last call (6r per pair test, 12r per rotation).
 double jacobi_flops_read_reset(cudaStream_t st);
 // X[k*m + i] = U[i*r + k] for i < r, 0 for r <= i < m  (k < r): [U; 0] stored column-major.

@@ -284,6 +284,140 @@ __global__ void jacobi_kernel(double* W, double* V, int batch, int r, int rp, in
   }
 }
 
+// Same sweeps with one 128-thread block per column pair: every thread holds MAXE rows of the
+// two columns of W and of V in registers (loads issued together), the three dot products are
+// reduced across the block, and the rotation is applied in registers before the stores.
+// Requires r <= 128 * MAXE.
+// W holds n columns of length m per matrix (column-major, stride m*n), V n columns of length n.
+template <int MAXE>
+__global__ void __launch_bounds__(128) jacobi_team_kernel(double* W, double* V, int batch, int m, int r, int rp,
+                                                           int max_sweeps, double tol, int* flags, int* conv,
+                                                           int* sweeps_out, const double* frob2, double* flop_acc,
+                                                           Sync s) {
+  __shared__ double red[3][4];
+  const int t = threadIdx.x, lane = t % 32, warp = t / 32;
+  const int npairs = rp / 2;
+  const int64_t tasks = (int64_t)batch * npairs;
+  const int64_t mr = (int64_t)m * r, rr = (int64_t)r * r;
+  double my_flops = 0.0;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    int* fl = flags + (sweep % 3) * batch;
+    if (blockIdx.x == 0) {
+      int* nxt = flags + ((sweep + 1) % 3) * batch;
+      for (int b = t; b < batch; b += blockDim.x) nxt[b] = 0;
+      __threadfence();
+    }
+    for (int round = 0; round < rp - 1; ++round) {
+      for (int64_t task = blockIdx.x; task < tasks; task += gridDim.x) {
+        const int b = (int)(task / npairs);
+        if (__ldcg(conv + b)) continue;
+        int p, q;
+        rr_pair(round, (int)(task % npairs), rp, p, q);
+        if (p >= r || q >= r) continue;
+        double* ap = W + b * mr + (int64_t)p * m;
+        double* aq = W + b * mr + (int64_t)q * m;
+        double* vp = V + b * rr + (int64_t)p * r;
+        double* vq = V + b * rr + (int64_t)q * r;
+        double x[MAXE], y[MAXE], u[MAXE], w[MAXE];
+#pragma unroll
+        for (int e = 0; e < MAXE; ++e) {
+          const int i = t + 128 * e;
+          x[e] = i < m ? __ldcg(ap + i) : 0.0;
+          y[e] = i < m ? __ldcg(aq + i) : 0.0;
+          u[e] = i < r ? __ldcg(vp + i) : 0.0;
+          w[e] = i < r ? __ldcg(vq + i) : 0.0;
+        }
+        double al = 0.0, be = 0.0, ga = 0.0;
+#pragma unroll
+        for (int e = 0; e < MAXE; ++e) {
+          al = fma(x[e], x[e], al);
+          be = fma(y[e], y[e], be);
+          ga = fma(x[e], y[e], ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (lane == 0) {
+          red[0][warp] = al;
+          red[1][warp] = be;
+          red[2][warp] = ga;
+        }
+        __syncthreads();
+        al = red[0][0] + red[0][1] + red[0][2] + red[0][3];
+        be = red[1][0] + red[1][1] + red[1][2] + red[1][3];
+        ga = red[2][0] + red[2][1] + red[2][2] + red[2][3];
+        __syncthreads();
+        const double floor2 = 1e-32 * __ldcg(frob2 + b);
+        if (t == 0) my_flops += 6.0 * m;
+        if (al > floor2 && be > floor2 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+          if (t == 0) my_flops += 6.0 * m + 6.0 * r;
+          double zeta = (be - al) / (2.0 * ga);
+          double tt;
+          if (fabs(zeta) > 1e150)
+            tt = 0.5 / zeta;
+          else
+            tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + tt * tt);
+          const double sn = c * tt;
+#pragma unroll
+          for (int e = 0; e < MAXE; ++e) {
+            const int i = t + 128 * e;
+            if (i < m) {
+              ap[i] = c * x[e] - sn * y[e];
+              aq[i] = sn * x[e] + c * y[e];
+            }
+            if (i < r) {
+              vp[i] = c * u[e] - sn * w[e];
+              vq[i] = sn * u[e] + c * w[e];
+            }
+          }
+          if (t == 0) fl[b] = 1;
+        }
+      }
+      if (!grid_barrier(s)) {
+        if (t == 0) atomicAdd(flop_acc, my_flops);
+        return;
+      }
+    }
+    int all = 1;
+    {
+      volatile int* vf = fl;
+      volatile int* vc = conv;
+      for (int b = 0; b < batch; ++b)
+        if (!vc[b] && vf[b] != 0) all = 0;
+    }
+    if (!grid_barrier(s)) {
+      if (t == 0) atomicAdd(flop_acc, my_flops);
+      return;
+    }
+    if (blockIdx.x == 0 && t == 0) {
+      volatile int* vf = fl;
+      for (int b = 0; b < batch; ++b)
+        if (vf[b] == 0) conv[b] = 1;
+      __threadfence();
+    }
+    if (!grid_barrier(s)) {
+      if (t == 0) atomicAdd(flop_acc, my_flops);
+      return;
+    }
+    if (all) {
+      ++sweep;
+      break;
+    }
+  }
+  if (t == 0) atomicAdd(flop_acc, my_flops);
+  if (blockIdx.x == 0 && t == 0) {
+    atomicAdd(sweeps_out, sweep);
+    for (int b = 0; b < batch; ++b)
+      if (!conv[b]) atomicOr(s.status, DEV_SVD_NOCONV);
+  }
+}
+
+// Launch the Jacobi sweeps (cooperative) with the register-resident team kernel.
+void launch_jacobi(double* W, double* V, int batch, int m, int r, int max_sweeps, int* flags, int* conv,
+                   int* sweeps_out, double* frob2, double* facc, const Sync& sy, cudaStream_t st);
+
 // Column norms, descending order, normalised left vectors.  One block per matrix.
 __global__ void svd_finalize_kernel(const double* W, const double* V, double* lam, double* Uo, double* Vo, int r,
                                     int* status) {
@@ -319,6 +453,75 @@ __global__ void svd_finalize_kernel(const double* W, const double* V, double* la
     Uo[b * rr + (int64_t)i * r + rank[k]] = Wb[e] * inv;
     Vo[b * rr + (int64_t)i * r + rank[k]] = Vb[e];
   }
+}
+
+// Finalize of the Jacobi SVD of B^t (m x l, column-major W; V l x l column-major), where
+// B = V W^t.  Sorted descending: lam[rank], Vm (m x ldv row-major, first l columns) = W_k / lam_k,
+// Ul (l x l row-major) = V's column k; flags[b] = 1 when the smallest value is not below
+// 1e-14 lam_max (the sketch may have missed directions).
+__global__ void svd_rect_finalize_kernel(const double* W, const double* V, double* lam, double* Vm, int64_t ldv,
+                                         double* Ul, int m, int l, int* incomplete, int* status) {
+  extern __shared__ double sm[];
+  double* nrm = sm;
+  int* rank = (int*)(sm + l);
+  const int b = blockIdx.x;
+  const double* Wb = W + (int64_t)b * m * l;
+  const double* Vb = V + (int64_t)b * l * l;
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nwarp = blockDim.x / 32;
+  for (int k = warp; k < l; k += nwarp) {
+    double s2 = 0.0;
+    for (int i = lane; i < m; i += 32) s2 = fma(Wb[(int64_t)k * m + i], Wb[(int64_t)k * m + i], s2);
+    s2 = warp_sum(s2);
+    if (lane == 0) {
+      nrm[k] = sqrt(s2);
+      if (!isfinite(s2)) atomicOr(status, DEV_NONFINITE);
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < l; k += blockDim.x) {
+    int rk = 0;
+    double v = nrm[k];
+    for (int j = 0; j < l; ++j) rk += (nrm[j] > v) || (nrm[j] == v && j < k);
+    rank[k] = rk;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0, mn = 1e308;
+    for (int k = 0; k < l; ++k) {
+      mx = fmax(mx, nrm[k]);
+      mn = fmin(mn, nrm[k]);
+    }
+    incomplete[b] = (mn > 1e-14 * mx) ? 1 : 0;
+  }
+  for (int k = threadIdx.x; k < l; k += blockDim.x) lam[(int64_t)b * m + rank[k]] = nrm[k];
+  for (int64_t e = threadIdx.x; e < (int64_t)m * l; e += blockDim.x) {
+    int k = (int)(e / m), i = (int)(e % m);
+    double inv = nrm[k] > 0.0 ? 1.0 / nrm[k] : 0.0;
+    Vm[(int64_t)b * m * ldv + (int64_t)i * ldv + rank[k]] = Wb[e] * inv;
+  }
+  for (int64_t e = threadIdx.x; e < (int64_t)l * l; e += blockDim.x) {
+    int k = (int)(e / l), j = (int)(e % l);
+    Ul[(int64_t)b * l * l + (int64_t)j * l + rank[k]] = Vb[e];
+  }
+}
+
+// Deterministic test matrix: splitmix64 of the element index, mapped to (-1, 1).
+__global__ void sketch_omega_kernel(double* O, int64_t n, uint64_t seed) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed + (uint64_t)e * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    O[e] = ((double)(z >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0;
+  }
+}
+
+// X (r x l column-major) = [I_l; 0]
+__global__ void eye_rect_kernel(double* X, int r, int l) {
+  const int b = blockIdx.y;
+  int64_t n = (int64_t)r * l;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    X[b * n + e] = ((e / r) == (e % r)) ? 1.0 : 0.0;
 }
 
 __global__ void identity_kernel(double* V, int r) {
@@ -369,7 +572,33 @@ int coop_grid(const void* kernel, int threads) {
   CTM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   CTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0));
   CTM_CHECK(per_sm > 0, CTM_ERR_CUDA, "cooperative kernel cannot be resident");
-  return sms * std::min(per_sm, 4);
+  return sms * per_sm;
+}
+
+template <int MAXE>
+void launch_jacobi_t(double* W, double* V, int batch, int m, int r, int max_sweeps, int* flags, int* conv,
+                     int* sweeps_out, double* frob2, double* facc, const Sync& sy, cudaStream_t st) {
+  const int threads = 128;
+  int rp = r + (r & 1);
+  int grid = coop_grid((const void*)jacobi_team_kernel<MAXE>, threads);
+  int64_t need = (int64_t)batch * (rp / 2);
+  grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, need));
+  double tol = 2.220446049250313e-16 * std::max(m, r);
+  Sync s = sy;
+  void* args[] = {&W, &V, &batch, &m, &r, &rp, &max_sweeps, &tol, &flags, &conv, &sweeps_out, &frob2, &facc, &s};
+  CTM_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_team_kernel<MAXE>, grid, threads, args, 0, st));
+  CTM_LAUNCHED();
+}
+
+void launch_jacobi(double* W, double* V, int batch, int m, int r, int max_sweeps, int* flags, int* conv,
+                   int* sweeps_out, double* frob2, double* facc, const Sync& sy, cudaStream_t st) {
+  const int e = std::max(m, r);
+  CTM_CHECK(e <= 128 * 16, CTM_ERR_INVALID_ARG, "Jacobi SVD: size too large");
+  if (e <= 256) launch_jacobi_t<2>(W, V, batch, m, r, max_sweeps, flags, conv, sweeps_out, frob2, facc, sy, st);
+  else if (e <= 512) launch_jacobi_t<4>(W, V, batch, m, r, max_sweeps, flags, conv, sweeps_out, frob2, facc, sy, st);
+  else if (e <= 768) launch_jacobi_t<6>(W, V, batch, m, r, max_sweeps, flags, conv, sweeps_out, frob2, facc, sy, st);
+  else if (e <= 1024) launch_jacobi_t<8>(W, V, batch, m, r, max_sweeps, flags, conv, sweeps_out, frob2, facc, sy, st);
+  else launch_jacobi_t<16>(W, V, batch, m, r, max_sweeps, flags, conv, sweeps_out, frob2, facc, sy, st);
 }
 
 }  // namespace
@@ -409,6 +638,84 @@ void qr_apply_Q(const double* A, const double* tau, double* X, int batch, int m,
   CTM_LAUNCHED();
 }
 
+// Truncated SVD of r x r matrices of low numerical rank by a sketched range finder
+// (Halko, Martinsson & Tropp 2011, Alg. 4.1, Gaussian-like test matrix) followed by the
+// one-sided Jacobi SVD of the l x r projection.  Wc: batch x r x r column-major M (kept).
+// On exit lam (batch x r, descending, zero beyond l), Uo / Vo (batch x r x r row-major,
+// zero beyond column l).  incomplete_host[b] = 1 where the sketch did not reach the
+// rounding floor (1e-14 lam_max): those matrices need the full SVD.
+void svd_sketch(const double* Wc, int batch, int r, int l, double* lam, double* Uo, double* Vo, int* status,
+                int* sweeps_out, std::vector<int>& incomplete_host, cudaStream_t st) {
+  const int64_t rr = (int64_t)r * r, rl = (int64_t)r * l, ll = (int64_t)l * l;
+  static thread_local double* ws = nullptr;
+  static thread_local size_t cap = 0;
+  static thread_local double* omega = nullptr;
+  static thread_local int64_t omega_n = 0;
+  const size_t need = sizeof(double) * (size_t)batch * (5 * rl + 3 * ll + l) + sizeof(int) * 2 * batch + 4096;
+  if (need > cap) {
+    if (ws) CTM_CUDA(cudaFree(ws));
+    cap = std::max(need, size_t(32) << 20);
+    CTM_CUDA(cudaMalloc(&ws, cap));
+  }
+  if (omega_n < rl) {
+    if (omega) CTM_CUDA(cudaFree(omega));
+    CTM_CUDA(cudaMalloc(&omega, sizeof(double) * rl));
+    omega_n = rl;
+    sketch_omega_kernel<<<256, 256, 0, st>>>(omega, rl, 0x2512144140ull);
+    CTM_LAUNCHED();
+  }
+  double* Y = ws;                       // r x l row-major
+  double* Z = Y + batch * rl;           // r x l row-major
+  double* Yt = Z + batch * rl;          // l x r row-major = Y column-major
+  double* Qc = Yt + batch * rl;         // Q column-major (r x l)
+  double* Bt = Qc + batch * rl;         // B = Q^t M, l x r row-major = B^t column-major
+  double* Vl = Bt + batch * rl;         // l x l Jacobi rotation (column-major)
+  double* Ul = Vl + batch * ll;         // l x l sorted
+  double* tau = Ul + batch * ll;        // l per matrix
+  int* inc = (int*)(tau + batch * l);
+  GemmSpec g;
+  // Y = M Omega (M = Wc^t), stored column-major: Y^t = Omega^t M^t = Omega^t Wc.  No power
+  // iteration: l exceeds the numerical rank (checked below), so range(M Omega) already holds every
+  // direction above the rounding floor, and powers of M would only widen the dynamic range.
+  g = GemmSpec();
+  g.M = l; g.N = r; g.K = r; g.batch = batch; g.transA = true; g.lda = l; g.ldb = r; g.ldc = r;
+  g.strideA = 0; g.strideB = rr; g.strideC = rl;
+  gemm_f64(omega, Wc, Yt, g, st);
+  // orthonormal basis of range(Y): Householder QR, Q formed explicitly
+  qr_householder(Yt, tau, batch, r, l, rl, status, st);
+  eye_rect_kernel<<<dim3((unsigned)std::min<int64_t>(4096, (rl + 255) / 256), batch), 256, 0, st>>>(Qc, r, l);
+  CTM_LAUNCHED();
+  qr_apply_Q(Yt, tau, Qc, batch, r, l, l, rl, rl, status, st);
+  // B^t (column-major r x l) = B row-major (l x r) = Q^t M = Qc^t Wc^t -> row-major: (Qc^t)(Wc^t)
+  g = GemmSpec();
+  g.M = l; g.N = r; g.K = r; g.batch = batch; g.transA = false; g.lda = r; g.transB = true; g.ldb = r; g.ldc = r;
+  g.strideA = rl; g.strideB = rr; g.strideC = rl;
+  gemm_f64(Qc, Wc, Bt, g, st);
+  // one-sided Jacobi on the l columns (length r) of B^t
+  ensure_coop(batch, st);
+  CTM_CUDA(cudaMemsetAsync(g_coop.flags, 0, 3 * batch * sizeof(int), st));
+  CTM_CUDA(cudaMemsetAsync(g_coop.conv, 0, batch * sizeof(int), st));
+  set_identity_colmajor(Vl, batch, l, st);
+  frob2_kernel<<<batch, 256, 0, st>>>(Bt, rl, g_coop.frob2);
+  CTM_LAUNCHED();
+  Sync s{g_coop.bar, g_coop.abort, status};
+  launch_jacobi(Bt, Vl, batch, r, l, 60, g_coop.flags, g_coop.conv, sweeps_out, g_coop.frob2, g_coop.flop_acc, s, st);
+  CTM_CUDA(cudaMemsetAsync(Uo, 0, sizeof(double) * batch * rr, st));
+  CTM_CUDA(cudaMemsetAsync(Vo, 0, sizeof(double) * batch * rr, st));
+  CTM_CUDA(cudaMemsetAsync(lam, 0, sizeof(double) * batch * r, st));
+  size_t smem = (size_t)l * (sizeof(double) + sizeof(int));
+  svd_rect_finalize_kernel<<<batch, 256, smem, st>>>(Bt, Vl, lam, Vo, r, Ul, r, l, inc, status);
+  CTM_LAUNCHED();
+  // U (first l columns of Uo, row-major ld r) = Q Ul
+  g = GemmSpec();
+  g.M = r; g.N = l; g.K = l; g.batch = batch; g.transA = true; g.lda = r; g.ldb = l; g.ldc = r;
+  g.strideA = rl; g.strideB = ll; g.strideC = rr;
+  gemm_f64(Qc, Ul, Uo, g, st);
+  incomplete_host.assign(batch, 0);
+  CTM_CUDA(cudaMemcpyAsync(incomplete_host.data(), inc, sizeof(int) * batch, cudaMemcpyDeviceToHost, st));
+  CTM_CUDA(cudaStreamSynchronize(st));
+}
+
 double jacobi_flops_read_reset(cudaStream_t st) {
   if (!g_coop.flop_acc) return 0.0;
   double v = 0.0;
@@ -431,22 +738,11 @@ void svd_jacobi(double* W, double* V, double* lam, double* Uo, double* Vo, int b
   ensure_coop(batch, st);
   CTM_CUDA(cudaMemsetAsync(g_coop.flags, 0, 3 * batch * sizeof(int), st));
   CTM_CUDA(cudaMemsetAsync(g_coop.conv, 0, batch * sizeof(int), st));
-  const int threads = 256;
-  int rp = r + (r & 1);
-  int grid = coop_grid((const void*)jacobi_kernel, threads);
-  int64_t need = ((int64_t)batch * (rp / 2) + threads / 32 - 1) / (threads / 32);
-  grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, need));
-  double tol = 2.220446049250313e-16 * r;
   Sync s{g_coop.bar, g_coop.abort, status};
-  int* flags = g_coop.flags;
-  int* conv = g_coop.conv;
-  double* frob2 = g_coop.frob2;
-  frob2_kernel<<<batch, 256, 0, st>>>(W, (int64_t)r * r, frob2);
+  frob2_kernel<<<batch, 256, 0, st>>>(W, (int64_t)r * r, g_coop.frob2);
   CTM_LAUNCHED();
-  double* facc = g_coop.flop_acc;
-  void* args[] = {&W, &V, &batch, &r, &rp, &max_sweeps, &tol, &flags, &conv, &sweeps_out, &frob2, &facc, &s};
-  CTM_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, grid, threads, args, 0, st));
-  CTM_LAUNCHED();
+  launch_jacobi(W, V, batch, r, r, max_sweeps, g_coop.flags, g_coop.conv, sweeps_out, g_coop.frob2, g_coop.flop_acc, s,
+                st);
   size_t smem = (size_t)r * (sizeof(double) + sizeof(int));
   if (smem > 48 * 1024) CTM_CUDA(cudaFuncSetAttribute(svd_finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   svd_finalize_kernel<<<batch, 256, smem, st>>>(W, V, lam, Uo, Vo, r, status);
@@ -516,17 +812,8 @@ void svd_noalloc(const double* M, int batch, int r, double* U, double* sv, doubl
   set_identity_colmajor(Vw, batch, r, st);
   frob2_kernel<<<batch, 256, 0, st>>>(W, rr, frob2);
   CTM_LAUNCHED();
-  const int threads = 256;
-  int rp = r + (r & 1);
-  int grid = coop_grid((const void*)jacobi_kernel, threads);
-  int64_t need = ((int64_t)batch * (rp / 2) + threads / 32 - 1) / (threads / 32);
-  grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, need));
-  double tol = 2.220446049250313e-16 * r;
-  int max_sweeps = 60;
   Sync s{bar, abort_flag, status};
-  void* args[] = {&W, &Vw, &batch, &r, &rp, &max_sweeps, &tol, &flags, &conv, &sweeps, &frob2, &facc, &s};
-  CTM_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, grid, threads, args, 0, st));
-  CTM_LAUNCHED();
+  launch_jacobi(W, Vw, batch, r, r, 60, flags, conv, sweeps, frob2, facc, s, st);
   size_t smem = (size_t)r * (sizeof(double) + sizeof(int));
   svd_finalize_kernel<<<batch, 256, smem, st>>>(W, Vw, sv, U, V, r, status);
   CTM_LAUNCHED();

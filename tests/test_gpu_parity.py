@@ -86,3 +86,22 @@ def test_batched_svd_entry_point():
             assert np.allclose(s[k], ref, rtol=1e-12, atol=1e-14 * ref[0])
             assert np.abs(U[k] @ np.diag(s[k]) @ V[k].T - M[k]).max() < 1e-13 * ref[0]
             assert np.abs(V[k].T @ V[k] - np.eye(r)).max() < 1e-13
+
+
+@pytest.mark.parametrize("name,n_iter", [("heis_d2_chi8", 20), ("heis_d4_chi32", 10)])
+def test_mixed_tf32x3_matches_oracle(name, n_iter):
+    # mixed mode: contractions on the tensor cores (error-compensated TF32), decompositions FP64
+    w = W.config(name)
+    E, g, _ = gpu_energy_grad(w, n_iter, precision="tf32x3")
+    Er, gr = oracle_energy_grad(w, n_iter)
+    assert abs(E - Er) <= 1e-6, (E, Er)
+    assert rel_l2(g, gr) <= 1e-3
+
+
+def test_plain_tf32_and_bf16_run_and_stay_close_in_energy():
+    # the uncompensated modes are faster but coarser: their energy is reported, not held to 1e-6
+    w = W.config("heis_d2_chi8")
+    Er, _ = oracle_energy_grad(w, w.n_iter, grad=False)
+    for prec, tol in (("tf32", 1e-3), ("bf16", 1e-2)):
+        E, _, _ = gpu_energy_grad(w, w.n_iter, precision=prec)
+        assert abs(E - Er) <= tol, (prec, E, Er)

@@ -168,7 +168,7 @@ def test_trivial_boundary_is_a_fixed_point_of_the_nested_iteration():
 
 # ----------------------------------------------------------------------------- single vs double
 @pytest.mark.parametrize("Lx,Ly", [(1, 1), (2, 2)])
-@pytest.mark.parametrize("cutoff,tol", [(1e-6, 1e-5), (1e-10, 1e-7)])
+@pytest.mark.parametrize("cutoff,tol", [(1e-5, 1e-5), (1e-10, 1e-7)])
 def test_single_and_double_layer_agree(Lx, Ly, cutoff, tol, monkeypatch):
     # Appendix: nested and reduced contraction agree once chi is large enough;
     # what is left is the truncation of the spectra at the cutoff.

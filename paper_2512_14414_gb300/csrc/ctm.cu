@@ -124,9 +124,10 @@ struct ctm_handle {
   double* env0 = nullptr;                          // FP64 copy of the initial environment
   std::vector<std::vector<std::array<ctm::Tensor, 8>>> ckpt;  // environment at the start of each iteration
   struct Fac {
-    double *U = nullptr, *V = nullptr, *lam = nullptr;
+    double *U = nullptr, *V = nullptr, *lam = nullptr;  // U, V: n_r x rs row-major; lam: rs
     int64_t n_r = 0;
-    int r = 0;
+    int r = 0;   // min(n_r, n_l): rank bound of rho
+    int rs = 0;  // singular triplets stored (r, or the sketch width l)
   };
   std::vector<std::vector<Fac>> fac;  // [iteration][projector pair]
   int iters_done = 0;
@@ -363,6 +364,77 @@ struct PairIn {
   std::vector<int64_t> pdims, qdims;  // dims of P and Q tensors [chi, b..., chi]
 };
 
+// Full factorisation of rho = N S^t for every pair of the batch: Householder QR of tall N and S
+// (rho = Q_n R_n R_s^t Q_s^t), one-sided Jacobi SVD of the r x r core, U/V lifted back through
+// the Q factors.  Stores r singular triplets per pair.
+void projectors_full(ctm_handle* h, const std::vector<PairIn>& in, const std::vector<Tensor>& N64,
+                     const std::vector<Tensor>& S64, std::vector<ctm_handle::Fac*>& F, int r) {
+  Engine& E = *h->eng;
+  cudaStream_t st = h->st;
+  const int nb = (int)in.size();
+  const int64_t rr = (int64_t)r * r;
+  double* W = (double*)E.arena().alloc(sizeof(double) * rr * nb);
+  double* Vw = (double*)E.arena().alloc(sizeof(double) * rr * nb);
+  double* lam = (double*)E.arena().alloc(sizeof(double) * r * nb);
+  double* Uo = (double*)E.arena().alloc(sizeof(double) * rr * nb);
+  double* Vo = (double*)E.arena().alloc(sizeof(double) * rr * nb);
+  std::vector<double*> Nc(nb, nullptr), Sc(nb, nullptr), tn(nb, nullptr), ts(nb, nullptr);
+  for (int b = 0; b < nb; ++b) {
+    const int64_t nr = in[b].n_r, nl = in[b].n_l;
+    GemmSpec g;
+    if (nr > nl) {  // tall: Householder QR of N and S (column-major copies)
+      Nc[b] = (double*)E.arena().alloc(sizeof(double) * nr * nl);
+      Sc[b] = (double*)E.arena().alloc(sizeof(double) * nr * nl);
+      tn[b] = (double*)E.arena().alloc(sizeof(double) * nl);
+      ts[b] = (double*)E.arena().alloc(sizeof(double) * nl);
+      PermSpec ps;
+      ps.rank = 2;
+      ps.out_dims[0] = nl;
+      ps.out_dims[1] = nr;
+      ps.in_stride[0] = 1;
+      ps.in_stride[1] = nl;
+      permute(N64[b].p, F64, Nc[b], F64, ps, false, 1.0, st);
+      permute(S64[b].p, F64, Sc[b], F64, ps, false, 1.0, st);
+      qr_householder(Nc[b], tn[b], 1, (int)nr, (int)nl, nr * nl, h->dstatus, st);
+      qr_householder(Sc[b], ts[b], 1, (int)nr, (int)nl, nr * nl, h->dstatus, st);
+      double* Rn = (double*)E.arena().alloc(sizeof(double) * nl * nl);
+      double* Rs = (double*)E.arena().alloc(sizeof(double) * nl * nl);
+      qr_extract_R(Nc[b], Rn, 1, (int)nr, (int)nl, nr * nl, st);
+      qr_extract_R(Sc[b], Rs, 1, (int)nr, (int)nl, nr * nl, st);
+      // W = (R_n R_s^t)^t = R_s R_n^t, i.e. M column-major
+      g.M = nl; g.N = nl; g.K = nl; g.transA = false; g.lda = nl; g.transB = true; g.ldb = nl; g.ldc = nl;
+      gemm_f64(Rs, Rn, W + b * rr, g, st);
+    } else {        // rho = N S^t is r x r: W = (N S^t)^t = S N^t
+      g.M = nr; g.N = nr; g.K = nl; g.transA = false; g.lda = nl; g.transB = true; g.ldb = nl; g.ldc = nr;
+      gemm_f64((const double*)S64[b].p, (const double*)N64[b].p, W + b * rr, g, st);
+    }
+  }
+  set_identity_colmajor(Vw, nb, r, st);
+  svd_jacobi(W, Vw, lam, Uo, Vo, nb, r, kMaxSweeps, h->dstatus, h->dsweeps, st);
+  for (int b = 0; b < nb; ++b) {
+    const int64_t nr = in[b].n_r, nl = in[b].n_l;
+    F[b]->rs = r;
+    CTM_CUDA(cudaMemcpyAsync(F[b]->lam, lam + (int64_t)b * r, sizeof(double) * r, cudaMemcpyDeviceToDevice, st));
+    if (nr > nl) {
+      for (int side = 0; side < 2; ++side) {
+        double* X = (double*)E.arena().alloc(sizeof(double) * nr * r);
+        embed_transpose((side ? Vo : Uo) + b * rr, r, X, nr, st);
+        qr_apply_Q(side ? Sc[b] : Nc[b], side ? ts[b] : tn[b], X, 1, (int)nr, (int)nl, r, nr * nl, nr * r, h->dstatus, st);
+        PermSpec ps;
+        ps.rank = 2;
+        ps.out_dims[0] = nr;
+        ps.out_dims[1] = r;
+        ps.in_stride[0] = 1;
+        ps.in_stride[1] = nr;
+        permute(X, F64, side ? F[b]->V : F[b]->U, F64, ps, false, 1.0, st);
+      }
+    } else {
+      CTM_CUDA(cudaMemcpyAsync(F[b]->U, Uo + b * rr, sizeof(double) * rr, cudaMemcpyDeviceToDevice, st));
+      CTM_CUDA(cudaMemcpyAsync(F[b]->V, Vo + b * rr, sizeof(double) * rr, cudaMemcpyDeviceToDevice, st));
+    }
+  }
+}
+
 void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, std::vector<Tensor>& Q) {
   Engine& E = *h->eng;
   cudaStream_t st = h->st;
@@ -397,59 +469,43 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
     }
   }
   if (!h->replay) {
-    const int64_t rr = (int64_t)r * r;
-    double* W = (double*)E.arena().alloc(sizeof(double) * rr * nb);
-    double* Vw = (double*)E.arena().alloc(sizeof(double) * rr * nb);
-    double* lam = (double*)E.arena().alloc(sizeof(double) * r * nb);
-    double* Uo = (double*)E.arena().alloc(sizeof(double) * rr * nb);
-    double* Vo = (double*)E.arena().alloc(sizeof(double) * rr * nb);
-    std::vector<double*> Nc(nb, nullptr), Sc(nb, nullptr), tn(nb, nullptr), ts(nb, nullptr);
-    for (int b = 0; b < nb; ++b) {
-      const int64_t nr = in[b].n_r, nl = in[b].n_l;
-      GemmSpec g;
-      if (nr > nl) {  // tall: Householder QR of N and S (column-major copies)
-        Nc[b] = (double*)E.arena().alloc(sizeof(double) * nr * nl);
-        Sc[b] = (double*)E.arena().alloc(sizeof(double) * nr * nl);
-        tn[b] = (double*)E.arena().alloc(sizeof(double) * nl);
-        ts[b] = (double*)E.arena().alloc(sizeof(double) * nl);
-        PermSpec ps;
-        ps.rank = 2;
-        ps.out_dims[0] = nl;
-        ps.out_dims[1] = nr;
-        ps.in_stride[0] = 1;
-        ps.in_stride[1] = nl;
-        permute(N64[b].p, F64, Nc[b], F64, ps, false, 1.0, st);
-        permute(S64[b].p, F64, Sc[b], F64, ps, false, 1.0, st);
-        qr_householder(Nc[b], tn[b], 1, (int)nr, (int)nl, nr * nl, h->dstatus, st);
-        qr_householder(Sc[b], ts[b], 1, (int)nr, (int)nl, nr * nl, h->dstatus, st);
-        double* Rn = (double*)E.arena().alloc(sizeof(double) * nl * nl);
-        double* Rs = (double*)E.arena().alloc(sizeof(double) * nl * nl);
-        qr_extract_R(Nc[b], Rn, 1, (int)nr, (int)nl, nr * nl, st);
-        qr_extract_R(Sc[b], Rs, 1, (int)nr, (int)nl, nr * nl, st);
-        // W = (R_n R_s^t)^t = R_s R_n^t, i.e. M column-major
-        g.M = nl; g.N = nl; g.K = nl; g.transA = false; g.lda = nl; g.transB = true; g.ldb = nl; g.ldc = nl;
-        gemm_f64(Rs, Rn, W + b * rr, g, st);
-      } else {        // rho = N S^t is r x r: W = (N S^t)^t = S N^t
-        g.M = nr; g.N = nr; g.K = nl; g.transA = false; g.lda = nl; g.transB = true; g.ldb = nl; g.ldc = nr;
-        gemm_f64((const double*)S64[b].p, (const double*)N64[b].p, W + b * rr, g, st);
-      }
-    }
-    // Truncated SVD through a sketch of width l when the matrices are large (Sec. Outlook:
-    // partial / randomised decompositions in Eq. QRSVD); exact whenever the numerical rank
-    // of M is below l, which is checked per matrix -- otherwise the full Jacobi SVD runs.
-    const int l = std::min(r, std::max(h->d.chi + 16, 32));
+    // Truncated SVD through a sketch of width l (Sec. Outlook: partial / randomised
+    // decompositions in Eq. QRSVD) taken directly on the product rho = N S^t; exact whenever
+    // the numerical rank of rho is below l, which is checked per matrix -- otherwise the full
+    // QR + Jacobi factorisation runs for the whole batch.
+    const int l = std::min(r, std::max(chi + 16, 32));
     bool sketched = false;
     if (h->debug_sweeps) CTM_CUDA(cudaMemsetAsync(h->dsweeps, 0, sizeof(int), st));
     if (2 * l <= r) {
-      std::vector<int> inc;
-      svd_sketch(W, nb, r, l, lam, Uo, Vo, h->dstatus, h->dsweeps, inc, st);
       sketched = true;
-      for (int x : inc) sketched = sketched && x == 0;
+      std::vector<char> done(nb, 0);
+      for (int b0 = 0; b0 < nb && sketched; ++b0) {
+        if (done[b0]) continue;
+        std::vector<int> grp;
+        for (int b = b0; b < nb; ++b)
+          if (!done[b] && in[b].n_r == in[b0].n_r && in[b].n_l == in[b0].n_l) grp.push_back(b), done[b] = 1;
+        const int nr = (int)in[b0].n_r, nl = (int)in[b0].n_l, ng = (int)grp.size();
+        std::vector<const double*> Np(ng), Sp(ng);
+        for (int g = 0; g < ng; ++g) Np[g] = (const double*)N64[grp[g]].p, Sp[g] = (const double*)S64[grp[g]].p;
+        double* ws = (double*)E.arena().alloc(svd_sketch_product_ws(ng, nr, nl, l));
+        double* lam = (double*)E.arena().alloc(sizeof(double) * ng * l);
+        double* Uo = (double*)E.arena().alloc(sizeof(double) * ng * (int64_t)nr * l);
+        double* Vo = (double*)E.arena().alloc(sizeof(double) * ng * (int64_t)nr * l);
+        std::vector<int> inc;
+        svd_sketch_product(Np.data(), Sp.data(), ng, nr, nl, l, ws, lam, Uo, Vo, h->dstatus, h->dsweeps, inc, st);
+        for (int x : inc) sketched = sketched && x == 0;
+        if (!sketched) break;
+        for (int g = 0; g < ng; ++g) {
+          ctm_handle::Fac* f = F[grp[g]];
+          f->rs = l;
+          const size_t nb_uv = sizeof(double) * (size_t)nr * l;
+          CTM_CUDA(cudaMemcpyAsync(f->lam, lam + (int64_t)g * l, sizeof(double) * l, cudaMemcpyDeviceToDevice, st));
+          CTM_CUDA(cudaMemcpyAsync(f->U, Uo + (int64_t)g * nr * l, nb_uv, cudaMemcpyDeviceToDevice, st));
+          CTM_CUDA(cudaMemcpyAsync(f->V, Vo + (int64_t)g * nr * l, nb_uv, cudaMemcpyDeviceToDevice, st));
+        }
+      }
     }
-    if (!sketched) {
-      set_identity_colmajor(Vw, nb, r, st);
-      svd_jacobi(W, Vw, lam, Uo, Vo, nb, r, kMaxSweeps, h->dstatus, h->dsweeps, st);
-    }
+    if (!sketched) projectors_full(h, in, N64, S64, F, r);
     if (h->debug_sweeps) {
       int sw = 0;
       CTM_CUDA(cudaMemcpyAsync(&sw, h->dsweeps, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -457,29 +513,8 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
       fprintf(stderr, "libctm: iteration %d pairs %d..%d r=%d %s l=%d Jacobi sweeps %d\n", h->cur_iter, h->cur_pair,
               h->cur_pair + nb - 1, r, sketched ? "sketch" : "full", l, sw);
     }
-    for (int b = 0; b < nb; ++b) {
-      const int64_t nr = in[b].n_r, nl = in[b].n_l;
-      CTM_CUDA(cudaMemcpyAsync(F[b]->lam, lam + (int64_t)b * r, sizeof(double) * r, cudaMemcpyDeviceToDevice, st));
-      if (nr > nl) {
-        for (int side = 0; side < 2; ++side) {
-          double* X = (double*)E.arena().alloc(sizeof(double) * nr * r);
-          embed_transpose((side ? Vo : Uo) + b * rr, r, X, nr, st);
-          qr_apply_Q(side ? Sc[b] : Nc[b], side ? ts[b] : tn[b], X, 1, (int)nr, (int)nl, r, nr * nl, nr * r, h->dstatus, st);
-          PermSpec ps;
-          ps.rank = 2;
-          ps.out_dims[0] = nr;
-          ps.out_dims[1] = r;
-          ps.in_stride[0] = 1;
-          ps.in_stride[1] = nr;
-          permute(X, F64, side ? F[b]->V : F[b]->U, F64, ps, false, 1.0, st);
-        }
-      } else {
-        CTM_CUDA(cudaMemcpyAsync(F[b]->U, Uo + b * rr, sizeof(double) * rr, cudaMemcpyDeviceToDevice, st));
-        CTM_CUDA(cudaMemcpyAsync(F[b]->V, Vo + b * rr, sizeof(double) * rr, cudaMemcpyDeviceToDevice, st));
-      }
-      // canonical signs keep the environment's chi basis fixed from one iteration to the next
-      sign_fix(F[b]->U, F[b]->V, 1, nr, r, st);
-    }
+    // canonical signs keep the environment's chi basis fixed from one iteration to the next
+    for (int b = 0; b < nb; ++b) sign_fix(F[b]->U, F[b]->V, 1, in[b].n_r, F[b]->rs, st);
   }
   // P = S^t V' L^-1/2, Q = N^t U' L^-1/2 (identical in forward and replay)
   struct Saved {
@@ -489,13 +524,14 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
   for (int b = 0; b < nb; ++b) {
     const int64_t nr = in[b].n_r, nl = in[b].n_l;
     Saved& s = sv[b];
+    const int rs = F[b]->rs;
     s.inv = (double*)E.arena().alloc(sizeof(double) * kept);
-    s.sinv = (double*)E.arena().alloc(sizeof(double) * r);
+    s.sinv = (double*)E.arena().alloc(sizeof(double) * rs);
     s.Wp = (double*)E.arena().alloc(sizeof(double) * nr * kept);
     s.Zp = (double*)E.arena().alloc(sizeof(double) * nr * kept);
-    proj_prepare(F[b]->lam, F[b]->U, F[b]->V, s.inv, s.sinv, 1, nr, r, kept, h->cut, kRankTol, h->dstatus, st);
-    scale_cols(F[b]->V, r, 0, s.inv, 0, s.Wp, 1, nr, kept, st);
-    scale_cols(F[b]->U, r, 0, s.inv, 0, s.Zp, 1, nr, kept, st);
+    proj_prepare(F[b]->lam, F[b]->U, F[b]->V, s.inv, s.sinv, 1, nr, rs, kept, h->cut, kRankTol, h->dstatus, st);
+    scale_cols(F[b]->V, rs, 0, s.inv, 0, s.Wp, 1, nr, kept, st);
+    scale_cols(F[b]->U, rs, 0, s.inv, 0, s.Zp, 1, nr, kept, st);
     Tensor P64 = E.zeros(F64, {nl, (int64_t)chi});
     Tensor Q64 = E.zeros(F64, {nl, (int64_t)chi});
     GemmSpec g;
@@ -526,12 +562,13 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
   const double eps = h->eps;
   const DType edt = h->edt;
   ctm_handle* hh = h;
-  E.push([hh, &E, inc, N64, S64, Fc, sv, Pc, Qc, r, kept, chi, eps, edt, st]() {
+  E.push([hh, &E, inc, N64, S64, Fc, sv, Pc, Qc, kept, chi, eps, edt, st]() {
     for (size_t b = 0; b < inc.size(); ++b) {
       void* gP = E.grad(Pc[b], false);
       void* gQ = E.grad(Qc[b], false);
       if (!gP && !gQ) continue;
       const int64_t nr = inc[b].n_r, nl = inc[b].n_l;
+      const int rs = Fc[b].rs;
       auto A64 = [&](int64_t n) { return (double*)E.arena().alloc(sizeof(double) * std::max<int64_t>(n, 1)); };
       double* dP = A64(nl * chi);
       double* dQ = A64(nl * chi);
@@ -561,46 +598,54 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
       double* dl = A64(kept);
       scale_cols(dZ, kept, 0, sv[b].inv, 0, dUk, 1, nr, kept, st);
       scale_cols(dW, kept, 0, sv[b].inv, 0, dVk, 1, nr, kept, st);
-      proj_dlam(dZ, U, dW, V, sv[b].inv, dl, 1, nr, r, kept, st);
-      double* Aa = A64((int64_t)r * kept);
-      double* Bb = A64((int64_t)r * kept);
+      proj_dlam(dZ, U, dW, V, sv[b].inv, dl, 1, nr, rs, kept, st);
+      double* Aa = A64((int64_t)rs * kept);
+      double* Bb = A64((int64_t)rs * kept);
       g = GemmSpec();
-      g.M = r; g.N = kept; g.K = nr; g.transA = true; g.lda = r; g.transB = false; g.ldb = kept; g.ldc = kept;
+      g.M = rs; g.N = kept; g.K = nr; g.transA = true; g.lda = rs; g.transB = false; g.ldb = kept; g.ldc = kept;
       gemm_f64(U, dUk, Aa, g, st);
       gemm_f64(V, dVk, Bb, g, st);
-      double* core = A64((int64_t)r * r);
-      proj_core(Aa, Bb, lam, dl, core, 1, r, kept, kRankTol, eps, st);
+      double* core = A64((int64_t)rs * rs);
+      proj_core(Aa, Bb, lam, dl, core, 1, rs, kept, kRankTol, eps, st);
       double* Xu = A64(nr * kept);
       double* Xv = A64(nr * kept);
       g = GemmSpec();
-      g.M = nr; g.N = kept; g.K = r; g.lda = r; g.ldb = kept; g.ldc = kept;
+      g.M = nr; g.N = kept; g.K = rs; g.lda = rs; g.ldb = kept; g.ldc = kept;
       gemm_f64(U, Aa, Xu, g, st);
       gemm_f64(V, Bb, Xv, g, st);
       double* Eu = A64(nr * kept);
       double* Ev = A64(nr * kept);
-      proj_resid(dUk, Xu, sv[b].sinv, Eu, 1, nr, r, kept, st);
-      proj_resid(dVk, Xv, sv[b].sinv, Ev, 1, nr, r, kept, st);
-      // drho = U core V^t + Eu V_k^t + U_k Ev^t
-      double* T1 = A64(nr * r);
-      double* drho = A64(nr * nr);
+      proj_resid(dUk, Xu, sv[b].sinv, Eu, 1, nr, rs, kept, st);
+      proj_resid(dVk, Xv, sv[b].sinv, Ev, 1, nr, rs, kept, st);
+      // drho = U core V^t + Eu V_k^t + U_k Ev^t is never formed (n_r x n_r); with
+      // VtS = V^t S and UtN = U^t N (rs x n_l):
+      //   dN += drho S   = U (core VtS + [Ev^t S; 0]) + Eu VtS[:kept]
+      //   dS += drho^t N = V (core^t UtN + [Eu^t N; 0]) + Ev UtN[:kept]
+      double* VtS = A64((int64_t)rs * nl);
+      double* UtN = A64((int64_t)rs * nl);
       g = GemmSpec();
-      g.M = nr; g.N = r; g.K = r; g.lda = r; g.ldb = r; g.ldc = r;
-      gemm_f64(U, core, T1, g, st);
+      g.M = rs; g.N = nl; g.K = nr; g.transA = true; g.lda = rs; g.ldb = nl; g.ldc = nl;
+      gemm_f64(V, S, VtS, g, st);
+      gemm_f64(U, N, UtN, g, st);
+      double* G1 = A64((int64_t)rs * nl);
+      double* G2 = A64((int64_t)rs * nl);
       g = GemmSpec();
-      g.M = nr; g.N = nr; g.K = r; g.lda = r; g.transB = true; g.ldb = r; g.ldc = nr;
-      gemm_f64(T1, V, drho, g, st);
-      g = GemmSpec();
-      g.M = nr; g.N = nr; g.K = kept; g.lda = kept; g.transB = true; g.ldb = r; g.ldc = nr; g.beta = 1.0;
-      gemm_f64(Eu, V, drho, g, st);
-      g = GemmSpec();
-      g.M = nr; g.N = nr; g.K = kept; g.lda = r; g.transB = true; g.ldb = kept; g.ldc = nr; g.beta = 1.0;
-      gemm_f64(U, Ev, drho, g, st);
-      // dN += drho S, dS += drho^t N
-      g = GemmSpec();
-      g.M = nr; g.N = nl; g.K = nr; g.lda = nr; g.ldb = nl; g.ldc = nl; g.beta = 1.0;
-      gemm_f64(drho, S, dN, g, st);
+      g.M = rs; g.N = nl; g.K = rs; g.lda = rs; g.ldb = nl; g.ldc = nl;
+      gemm_f64(core, VtS, G1, g, st);
       g.transA = true;
-      gemm_f64(drho, N, dS, g, st);
+      gemm_f64(core, UtN, G2, g, st);
+      g = GemmSpec();
+      g.M = kept; g.N = nl; g.K = nr; g.transA = true; g.lda = kept; g.ldb = nl; g.ldc = nl; g.beta = 1.0;
+      gemm_f64(Ev, S, G1, g, st);
+      gemm_f64(Eu, N, G2, g, st);
+      g = GemmSpec();
+      g.M = nr; g.N = nl; g.K = rs; g.lda = rs; g.ldb = nl; g.ldc = nl; g.beta = 1.0;
+      gemm_f64(U, G1, dN, g, st);
+      gemm_f64(V, G2, dS, g, st);
+      g = GemmSpec();
+      g.M = nr; g.N = nl; g.K = kept; g.lda = kept; g.ldb = nl; g.ldc = nl; g.beta = 1.0;
+      gemm_f64(Eu, VtS, dN, g, st);
+      gemm_f64(Ev, UtN, dS, g, st);
       if (inc[b].N.id >= 0) cast(dN, F64, E.grad(inc[b].N), edt, nr * nl, true, st);
       if (inc[b].S.id >= 0) cast(dS, F64, E.grad(inc[b].S), edt, nr * nl, true, st);
     }
@@ -934,7 +979,8 @@ void forward_iters(ctm_handle* h, int n_iter, double* delta_host) {
       auto& a = h->fac[it];
       auto& b = h->fac[it - 1];
       for (size_t p = 0; p < a.size() && p < b.size(); ++p)
-        spectrum_delta(a[p].lam, b[p].lam, 1, a[p].r, std::min(h->d.chi, a[p].r), h->dscal, h->st);
+        spectrum_delta(a[p].lam, b[p].lam, 1, std::min(a[p].rs, b[p].rs), std::min(h->d.chi, std::min(a[p].rs, b[p].rs)),
+                       h->dscal, h->st);
       CTM_CUDA(cudaMemcpyAsync(delta_host, h->dscal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
     }
   }

@@ -459,8 +459,8 @@ __global__ void svd_finalize_kernel(const double* W, const double* V, double* la
 // B = V W^t.  Sorted descending: lam[rank], Vm (m x ldv row-major, first l columns) = W_k / lam_k,
 // Ul (l x l row-major) = V's column k; flags[b] = 1 when the smallest value is not below
 // 1e-14 lam_max (the sketch may have missed directions).
-__global__ void svd_rect_finalize_kernel(const double* W, const double* V, double* lam, double* Vm, int64_t ldv,
-                                         double* Ul, int m, int l, int* incomplete, int* status) {
+__global__ void svd_rect_finalize_kernel(const double* W, const double* V, double* lam, int64_t lam_stride, double* Vm,
+                                         int64_t ldv, double* Ul, int m, int l, int* incomplete, int* status) {
   extern __shared__ double sm[];
   double* nrm = sm;
   int* rank = (int*)(sm + l);
@@ -493,7 +493,7 @@ __global__ void svd_rect_finalize_kernel(const double* W, const double* V, doubl
     }
     incomplete[b] = (mn > 1e-14 * mx) ? 1 : 0;
   }
-  for (int k = threadIdx.x; k < l; k += blockDim.x) lam[(int64_t)b * m + rank[k]] = nrm[k];
+  for (int k = threadIdx.x; k < l; k += blockDim.x) lam[(int64_t)b * lam_stride + rank[k]] = nrm[k];
   for (int64_t e = threadIdx.x; e < (int64_t)m * l; e += blockDim.x) {
     int k = (int)(e / m), i = (int)(e % m);
     double inv = nrm[k] > 0.0 ? 1.0 / nrm[k] : 0.0;
@@ -638,6 +638,21 @@ void qr_apply_Q(const double* A, const double* tau, double* X, int batch, int m,
   CTM_LAUNCHED();
 }
 
+// Test matrix of the sketches: element e is splitmix64(seed + e * golden) mapped to (-1, 1),
+// so a longer buffer extends a shorter one and every shape reads the same leading values.
+static const double* sketch_omega(int64_t n, cudaStream_t st) {
+  static thread_local double* omega = nullptr;
+  static thread_local int64_t omega_n = 0;
+  if (omega_n < n) {
+    if (omega) CTM_CUDA(cudaFree(omega));
+    CTM_CUDA(cudaMalloc(&omega, sizeof(double) * n));
+    omega_n = n;
+    sketch_omega_kernel<<<256, 256, 0, st>>>(omega, n, 0x2512144140ull);
+    CTM_LAUNCHED();
+  }
+  return omega;
+}
+
 // Truncated SVD of r x r matrices of low numerical rank by a sketched range finder
 // (Halko, Martinsson & Tropp 2011, Alg. 4.1, Gaussian-like test matrix) followed by the
 // one-sided Jacobi SVD of the l x r projection.  Wc: batch x r x r column-major M (kept).
@@ -649,21 +664,13 @@ void svd_sketch(const double* Wc, int batch, int r, int l, double* lam, double* 
   const int64_t rr = (int64_t)r * r, rl = (int64_t)r * l, ll = (int64_t)l * l;
   static thread_local double* ws = nullptr;
   static thread_local size_t cap = 0;
-  static thread_local double* omega = nullptr;
-  static thread_local int64_t omega_n = 0;
   const size_t need = sizeof(double) * (size_t)batch * (5 * rl + 3 * ll + l) + sizeof(int) * 2 * batch + 4096;
   if (need > cap) {
     if (ws) CTM_CUDA(cudaFree(ws));
     cap = std::max(need, size_t(32) << 20);
     CTM_CUDA(cudaMalloc(&ws, cap));
   }
-  if (omega_n < rl) {
-    if (omega) CTM_CUDA(cudaFree(omega));
-    CTM_CUDA(cudaMalloc(&omega, sizeof(double) * rl));
-    omega_n = rl;
-    sketch_omega_kernel<<<256, 256, 0, st>>>(omega, rl, 0x2512144140ull);
-    CTM_LAUNCHED();
-  }
+  const double* omega = sketch_omega(rl, st);
   double* Y = ws;                       // r x l row-major
   double* Z = Y + batch * rl;           // r x l row-major
   double* Yt = Z + batch * rl;          // l x r row-major = Y column-major
@@ -699,17 +706,88 @@ void svd_sketch(const double* Wc, int batch, int r, int l, double* lam, double* 
   frob2_kernel<<<batch, 256, 0, st>>>(Bt, rl, g_coop.frob2);
   CTM_LAUNCHED();
   Sync s{g_coop.bar, g_coop.abort, status};
-  launch_jacobi(Bt, Vl, batch, r, l, 60, g_coop.flags, g_coop.conv, sweeps_out, g_coop.frob2, g_coop.flop_acc, s, st);
+  {
+    ProfScope ps(PROF_SVD, st, 0.0, 8.0 * batch * rl * 4);
+    launch_jacobi(Bt, Vl, batch, r, l, 60, g_coop.flags, g_coop.conv, sweeps_out, g_coop.frob2, g_coop.flop_acc, s, st);
+  }
   CTM_CUDA(cudaMemsetAsync(Uo, 0, sizeof(double) * batch * rr, st));
   CTM_CUDA(cudaMemsetAsync(Vo, 0, sizeof(double) * batch * rr, st));
   CTM_CUDA(cudaMemsetAsync(lam, 0, sizeof(double) * batch * r, st));
   size_t smem = (size_t)l * (sizeof(double) + sizeof(int));
-  svd_rect_finalize_kernel<<<batch, 256, smem, st>>>(Bt, Vl, lam, Vo, r, Ul, r, l, inc, status);
+  svd_rect_finalize_kernel<<<batch, 256, smem, st>>>(Bt, Vl, lam, r, Vo, r, Ul, r, l, inc, status);
   CTM_LAUNCHED();
   // U (first l columns of Uo, row-major ld r) = Q Ul
   g = GemmSpec();
   g.M = r; g.N = l; g.K = l; g.batch = batch; g.transA = true; g.lda = r; g.ldb = l; g.ldc = r;
   g.strideA = rl; g.strideB = ll; g.strideC = rr;
+  gemm_f64(Qc, Ul, Uo, g, st);
+  incomplete_host.assign(batch, 0);
+  CTM_CUDA(cudaMemcpyAsync(incomplete_host.data(), inc, sizeof(int) * batch, cudaMemcpyDeviceToHost, st));
+  CTM_CUDA(cudaStreamSynchronize(st));
+}
+
+size_t svd_sketch_product_ws(int batch, int nr, int nl, int l) {
+  const size_t per = (size_t)2 * nl * l + (size_t)3 * nr * l + (size_t)2 * l * l + l;
+  return sizeof(double) * batch * per + sizeof(int) * batch + 256;
+}
+
+void svd_sketch_product(const double* const* N, const double* const* S, int batch, int nr, int nl, int l, double* ws,
+                        double* lam, double* Uo, double* Vo, int* status, int* sweeps_out, std::vector<int>& incomplete_host,
+                        cudaStream_t st) {
+  const int64_t Ln = (int64_t)nl * l, Lr = (int64_t)nr * l, ll = (int64_t)l * l;
+  const double* omega = sketch_omega(Lr, st);
+  double* T = ws;                    // S^t Omega, n_l x l row-major
+  double* Yt = T + batch * Ln;       // (N T)^t, l x n_r row-major = Y column-major
+  double* Qc = Yt + batch * Lr;      // Q column-major (n_r x l)
+  double* Z = Qc + batch * Lr;       // Q^t N, l x n_l row-major
+  double* Bt = Z + batch * Ln;       // B = Z S^t, l x n_r row-major = B^t column-major
+  double* Vl = Bt + batch * Lr;      // l x l Jacobi rotation (column-major)
+  double* Ul = Vl + batch * ll;      // l x l sorted
+  double* tau = Ul + batch * ll;     // l per matrix
+  int* inc = (int*)(tau + batch * l);
+  GemmSpec g;
+  for (int b = 0; b < batch; ++b) {
+    // T = S^t Omega
+    g = GemmSpec();
+    g.M = nl; g.N = l; g.K = nr; g.transA = true; g.lda = nl; g.ldb = l; g.ldc = l;
+    gemm_f64(S[b], omega, T + b * Ln, g, st);
+    // Y^t = T^t N^t
+    g = GemmSpec();
+    g.M = l; g.N = nr; g.K = nl; g.transA = true; g.lda = l; g.transB = true; g.ldb = nl; g.ldc = nr;
+    gemm_f64(T + b * Ln, N[b], Yt + b * Lr, g, st);
+  }
+  qr_householder(Yt, tau, batch, nr, l, Lr, status, st);
+  eye_rect_kernel<<<dim3((unsigned)std::min<int64_t>(4096, (Lr + 255) / 256), batch), 256, 0, st>>>(Qc, nr, l);
+  CTM_LAUNCHED();
+  qr_apply_Q(Yt, tau, Qc, batch, nr, l, l, Lr, Lr, status, st);
+  for (int b = 0; b < batch; ++b) {
+    // Z = Q^t N (Qc read row-major is Q^t)
+    g = GemmSpec();
+    g.M = l; g.N = nl; g.K = nr; g.lda = nr; g.ldb = nl; g.ldc = nl;
+    gemm_f64(Qc + b * Lr, N[b], Z + b * Ln, g, st);
+    // B = Z S^t
+    g = GemmSpec();
+    g.M = l; g.N = nr; g.K = nl; g.lda = nl; g.transB = true; g.ldb = nl; g.ldc = nr;
+    gemm_f64(Z + b * Ln, S[b], Bt + b * Lr, g, st);
+  }
+  ensure_coop(batch, st);
+  CTM_CUDA(cudaMemsetAsync(g_coop.flags, 0, 3 * batch * sizeof(int), st));
+  CTM_CUDA(cudaMemsetAsync(g_coop.conv, 0, batch * sizeof(int), st));
+  set_identity_colmajor(Vl, batch, l, st);
+  frob2_kernel<<<batch, 256, 0, st>>>(Bt, Lr, g_coop.frob2);
+  CTM_LAUNCHED();
+  Sync s{g_coop.bar, g_coop.abort, status};
+  {
+    ProfScope ps(PROF_SVD, st, 0.0, 8.0 * batch * Lr * 4);
+    launch_jacobi(Bt, Vl, batch, nr, l, 60, g_coop.flags, g_coop.conv, sweeps_out, g_coop.frob2, g_coop.flop_acc, s, st);
+  }
+  size_t smem = (size_t)l * (sizeof(double) + sizeof(int));
+  svd_rect_finalize_kernel<<<batch, 256, smem, st>>>(Bt, Vl, lam, l, Vo, l, Ul, nr, l, inc, status);
+  CTM_LAUNCHED();
+  // U = Q Ul (n_r x l row-major)
+  g = GemmSpec();
+  g.M = nr; g.N = l; g.K = l; g.batch = batch; g.transA = true; g.lda = nr; g.ldb = l; g.ldc = l;
+  g.strideA = Lr; g.strideB = ll; g.strideC = Lr;
   gemm_f64(Qc, Ul, Uo, g, st);
   incomplete_host.assign(batch, 0);
   CTM_CUDA(cudaMemcpyAsync(incomplete_host.data(), inc, sizeof(int) * batch, cudaMemcpyDeviceToHost, st));

@@ -43,15 +43,28 @@ FP64_PEAK_TFLOPS = 1.25
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
+def _die_with_parent():
+    """Child side of the nvidia-smi sampler: ask Linux to end it when bench.py ends, however it ends."""
+    try:
+        import ctypes
+        import signal
+        ctypes.CDLL("libc.so.6", use_errno=True).prctl(1, signal.SIGTERM)  # PR_SET_PDEATHSIG
+    except Exception:
+        pass
+
+
 class Clocks:
     """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
 
-    def __init__(self, index):
+    def __init__(self, index, enabled=True):
         self.index = index
+        self.enabled = enabled
         self.proc = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{index}.csv")
 
     def start(self):
+        if not self.enabled:
+            return
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
@@ -60,13 +73,15 @@ class Clocks:
                  "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL,
+                preexec_fn=_die_with_parent)
         except Exception:
             self.proc = None
 
     def stop(self):
         if not self.proc:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None,
+                    "reasons": ["not sampled (--no-clocks)" if not self.enabled else "nvidia-smi unavailable"]}
         self.proc.terminate()
         self.proc.wait()
         self.f.close()
@@ -115,7 +130,7 @@ def _roofline(prof, precision, peaks, peak_kind):
         return {"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None, "launches": n,
                 "peak_source": f"{peak_kind} bf16 sustained" + ("" if precision.startswith("bf16") else " x 1/2 (tf32)")}
-    fp64 = name in ("svd", "qr") or precision == "fp64"
+    fp64 = name in ("svd", "qr", "gemm_f64") or precision == "fp64"
     peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
     ach = fl / (ms * 1e-3) / 1e12
     return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
@@ -195,6 +210,7 @@ def main():
     ap.add_argument("--n-iter", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true", help="skip the nvidia-smi clock sampler (profiler runs)")
     args = ap.parse_args()
 
     import workloads as W
@@ -236,7 +252,7 @@ def main():
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    clocks = Clocks(local)
+    clocks = Clocks(local, enabled=not args.no_clocks)
     clocks.start()
     launches0 = ctm.kernel_launches
     ctm.profile(True)

@@ -145,8 +145,8 @@ int64_t ctm_kernel_launches(const ctm_handle* h);
  * event time (ms), the number of recorded launches and the algorithmic flops
  * and bytes of those launches (flops of the Jacobi SVD are counted on the
  * device: 6r per column-pair test and 12r per rotation).
- * Classes: 0 GEMM (SIMT), 1 permutation, 2 Jacobi SVD, 3 Householder QR,
- * 4 other, 5 tensor-core GEMM. */
+ * Classes: 0 FP32 GEMM (CUDA cores), 1 permutation, 2 Jacobi SVD,
+ * 3 Householder QR, 4 other, 5 tensor-core GEMM, 6 FP64 GEMM (CUDA cores). */
 int ctm_profile(ctm_handle* h, int enable);
 int ctm_profile_read(ctm_handle* h, int cls, double* ms, int64_t* launches, double* flops, double* bytes);
 

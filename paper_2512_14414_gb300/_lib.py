@@ -13,7 +13,7 @@ PRECISIONS = {"fp64": CTM_FP64, "tf32": CTM_TF32, "bf16": CTM_BF16, "tf32x3": CT
 EXPORTS = ["ctm_create", "ctm_init", "ctm_step", "ctm_energy", "ctm_grad", "ctm_get_env", "ctm_set_env",
            "ctm_env_numel", "ctm_kernel_launches", "ctm_profile", "ctm_profile_read", "ctm_svd", "ctm_svd_noalloc",
            "ctm_destroy", "ctm_error_string"]
-PROF_CLASSES = {"gemm": 0, "permute": 1, "svd": 2, "qr": 3, "misc": 4, "tc_gemm": 5}
+PROF_CLASSES = {"gemm": 0, "permute": 1, "svd": 2, "qr": 3, "misc": 4, "tc_gemm": 5, "gemm_f64": 6}
 
 
 class CtmTerm(ctypes.Structure):

@@ -49,22 +49,39 @@ inline void count_launch() {
 // Per-class device timing with CUDA events (enabled by ctm_profile).  A scope records an
 // event pair around the launches it encloses, on the launching stream.
 enum ProfClass : int { PROF_GEMM = 0, PROF_PERMUTE = 1, PROF_SVD = 2, PROF_QR = 3, PROF_MISC = 4, PROF_TC = 5,
-                       PROF_NCLASS = 6 };
+                       PROF_GEMM64 = 6, PROF_NCLASS = 7 };
 struct Profiler {
   bool on = false;
-  std::vector<cudaEvent_t> ev;  // pairs
+  std::vector<cudaEvent_t> ev;  // pairs, recycled once folded
   std::vector<int> cls;
   std::vector<double> flops, bytes;
+  std::vector<std::string> tags;  // per launch, only when dumping
   size_t used = 0;
-  void begin(int c, cudaStream_t st, double f, double b);
+  double ms[PROF_NCLASS] = {0}, fl[PROF_NCLASS] = {0}, by[PROF_NCLASS] = {0};
+  int64_t n[PROF_NCLASS] = {0};
+  FILE* dump = nullptr;  // per-launch records (CTM_PROF_DUMP=<path>): class, tag, ms
+  void begin(int c, cudaStream_t st, double f, double b, const char* tag);
   void end(cudaStream_t st);
+  void fold();   // waits for the recorded events and adds them to the class totals
+  void clear();  // totals to zero
+  ~Profiler();
 };
 extern thread_local Profiler* g_prof;
+inline bool prof_dumping() { return g_prof && g_prof->on && g_prof->dump; }
+// Shape tag of a launch for the per-launch dump ("" unless dumping).
+inline const char* prof_tag(const char* kind, int64_t b, int64_t m, int64_t n, int64_t k, int x = 0) {
+  static thread_local char buf[128];
+  if (!prof_dumping()) return nullptr;
+  snprintf(buf, sizeof buf, "%s b=%lld M=%lld N=%lld K=%lld x=%d", kind, (long long)b, (long long)m, (long long)n,
+           (long long)k, x);
+  return buf;
+}
 struct ProfScope {
   bool active;
   cudaStream_t st;
-  ProfScope(int c, cudaStream_t s, double f = 0, double b = 0) : active(g_prof && g_prof->on), st(s) {
-    if (active) g_prof->begin(c, s, f, b);
+  ProfScope(int c, cudaStream_t s, double f = 0, double b = 0, const char* tag = nullptr)
+      : active(g_prof && g_prof->on), st(s) {
+    if (active) g_prof->begin(c, s, f, b, tag);
   }
   ~ProfScope() {
     if (active) g_prof->end(st);

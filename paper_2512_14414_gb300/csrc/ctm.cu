@@ -130,6 +130,7 @@ struct ctm_handle {
     int rs = 0;  // singular triplets stored (r, or the sketch width l)
   };
   std::vector<std::vector<Fac>> fac;  // [iteration][projector pair]
+  std::vector<int> rank_hint;         // [projector pair] numerical rank of rho in the previous iteration (0: unknown)
   int iters_done = 0;
   int* dstatus = nullptr;
   int* dsweeps = nullptr;
@@ -137,8 +138,6 @@ struct ctm_handle {
   double *hs = nullptr, *coup = nullptr;
   std::string last_error;
   ctm::Profiler prof;
-  double prof_ms[ctm::PROF_NCLASS] = {0}, prof_flops[ctm::PROF_NCLASS] = {0}, prof_bytes[ctm::PROF_NCLASS] = {0};
-  int64_t prof_n[ctm::PROF_NCLASS] = {0};
   // replay state of the current iteration (backward recompute)
   bool replay = false;
   int cur_iter = 0, cur_pair = 0;
@@ -473,45 +472,71 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
     // decompositions in Eq. QRSVD) taken directly on the product rho = N S^t; exact whenever
     // the numerical rank of rho is below l, which is checked per matrix -- otherwise the full
     // QR + Jacobi factorisation runs for the whole batch.
-    const int l = std::min(r, std::max(chi + 16, 32));
+    // Width: the pair's numerical rank in the previous iteration plus a margin (chi + 16 when
+    // unknown); doubled once when the sketch misses the floor.
+    auto& hint = h->rank_hint;
+    if ((int)hint.size() < h->cur_pair + nb) hint.resize(h->cur_pair + nb, 0);
+    int l = std::min(r, std::max(chi + 16, 32));
     bool sketched = false;
     if (h->debug_sweeps) CTM_CUDA(cudaMemsetAsync(h->dsweeps, 0, sizeof(int), st));
-    if (2 * l <= r) {
-      sketched = true;
-      std::vector<char> done(nb, 0);
-      for (int b0 = 0; b0 < nb && sketched; ++b0) {
-        if (done[b0]) continue;
-        std::vector<int> grp;
-        for (int b = b0; b < nb; ++b)
-          if (!done[b] && in[b].n_r == in[b0].n_r && in[b].n_l == in[b0].n_l) grp.push_back(b), done[b] = 1;
-        const int nr = (int)in[b0].n_r, nl = (int)in[b0].n_l, ng = (int)grp.size();
-        std::vector<const double*> Np(ng), Sp(ng);
-        for (int g = 0; g < ng; ++g) Np[g] = (const double*)N64[grp[g]].p, Sp[g] = (const double*)S64[grp[g]].p;
+    std::vector<char> done(nb, 0);
+    sketched = true;
+    for (int b0 = 0; b0 < nb && sketched; ++b0) {
+      if (done[b0]) continue;
+      std::vector<int> grp;
+      for (int b = b0; b < nb; ++b)
+        if (!done[b] && in[b].n_r == in[b0].n_r && in[b].n_l == in[b0].n_l) grp.push_back(b), done[b] = 1;
+      const int nr = (int)in[b0].n_r, nl = (int)in[b0].n_l, ng = (int)grp.size();
+      int hmax = 0;
+      bool known = true;
+      for (int b : grp) hmax = std::max(hmax, hint[h->cur_pair + b]), known = known && hint[h->cur_pair + b] > 0;
+      l = known ? std::min(r, std::max(16, (hmax + 12 + 7) / 8 * 8)) : std::min(r, std::max(chi + 16, 32));
+      std::vector<const double*> Np(ng), Sp(ng);
+      for (int g = 0; g < ng; ++g) Np[g] = (const double*)N64[grp[g]].p, Sp[g] = (const double*)S64[grp[g]].p;
+      bool ok = false;
+      for (int attempt = 0; attempt < 2 && !ok && 2 * l <= r; ++attempt) {
         double* ws = (double*)E.arena().alloc(svd_sketch_product_ws(ng, nr, nl, l));
         double* lam = (double*)E.arena().alloc(sizeof(double) * ng * l);
         double* Uo = (double*)E.arena().alloc(sizeof(double) * ng * (int64_t)nr * l);
         double* Vo = (double*)E.arena().alloc(sizeof(double) * ng * (int64_t)nr * l);
-        std::vector<int> inc;
-        svd_sketch_product(Np.data(), Sp.data(), ng, nr, nl, l, ws, lam, Uo, Vo, h->dstatus, h->dsweeps, inc, st);
-        for (int x : inc) sketched = sketched && x == 0;
-        if (!sketched) break;
+        std::vector<int> inc, rk;
+        svd_sketch_product(Np.data(), Sp.data(), ng, nr, nl, l, ws, lam, Uo, Vo, h->dstatus, h->dsweeps, inc, rk, st);
+        ok = true;
+        for (int x : inc) ok = ok && x == 0;
+        if (!ok) {
+          l *= 2;
+          continue;
+        }
         for (int g = 0; g < ng; ++g) {
           ctm_handle::Fac* f = F[grp[g]];
           f->rs = l;
+          hint[h->cur_pair + grp[g]] = rk[g];
           const size_t nb_uv = sizeof(double) * (size_t)nr * l;
           CTM_CUDA(cudaMemcpyAsync(f->lam, lam + (int64_t)g * l, sizeof(double) * l, cudaMemcpyDeviceToDevice, st));
           CTM_CUDA(cudaMemcpyAsync(f->U, Uo + (int64_t)g * nr * l, nb_uv, cudaMemcpyDeviceToDevice, st));
           CTM_CUDA(cudaMemcpyAsync(f->V, Vo + (int64_t)g * nr * l, nb_uv, cudaMemcpyDeviceToDevice, st));
         }
       }
+      sketched = ok;
     }
+    if (!sketched)
+      for (int b = 0; b < nb; ++b) hint[h->cur_pair + b] = 0;
     if (!sketched) projectors_full(h, in, N64, S64, F, r);
     if (h->debug_sweeps) {
       int sw = 0;
       CTM_CUDA(cudaMemcpyAsync(&sw, h->dsweeps, sizeof(int), cudaMemcpyDeviceToHost, st));
       CTM_CUDA(cudaStreamSynchronize(st));
-      fprintf(stderr, "libctm: iteration %d pairs %d..%d r=%d %s l=%d Jacobi sweeps %d\n", h->cur_iter, h->cur_pair,
-              h->cur_pair + nb - 1, r, sketched ? "sketch" : "full", l, sw);
+      int rk_floor = 0, rk_cut = 0;  // largest numerical rank (1e-14) and kept count (cutoff) of the batch
+      for (int b = 0; b < nb; ++b) {
+        std::vector<double> lh(F[b]->rs);
+        CTM_CUDA(cudaMemcpy(lh.data(), F[b]->lam, sizeof(double) * lh.size(), cudaMemcpyDeviceToHost));
+        int a = 0, c = 0;
+        for (double v : lh) a += v > 1e-14 * lh[0], c += v > h->cut * lh[0];
+        rk_floor = std::max(rk_floor, a);
+        rk_cut = std::max(rk_cut, c);
+      }
+      fprintf(stderr, "libctm: iteration %d pairs %d..%d r=%d %s l=%d Jacobi sweeps %d rank %d above cutoff %d\n",
+              h->cur_iter, h->cur_pair, h->cur_pair + nb - 1, r, sketched ? "sketch" : "full", l, sw, rk_floor, rk_cut);
     }
     // canonical signs keep the environment's chi basis fixed from one iteration to the next
     for (int b = 0; b < nb; ++b) sign_fix(F[b]->U, F[b]->V, 1, in[b].n_r, F[b]->rs, st);
@@ -525,17 +550,18 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
     const int64_t nr = in[b].n_r, nl = in[b].n_l;
     Saved& s = sv[b];
     const int rs = F[b]->rs;
-    s.inv = (double*)E.arena().alloc(sizeof(double) * kept);
+    const int kb = std::min(kept, rs);  // triplets beyond the stored ones are below the rank floor
+    s.inv = (double*)E.arena().alloc(sizeof(double) * kb);
     s.sinv = (double*)E.arena().alloc(sizeof(double) * rs);
-    s.Wp = (double*)E.arena().alloc(sizeof(double) * nr * kept);
-    s.Zp = (double*)E.arena().alloc(sizeof(double) * nr * kept);
-    proj_prepare(F[b]->lam, F[b]->U, F[b]->V, s.inv, s.sinv, 1, nr, rs, kept, h->cut, kRankTol, h->dstatus, st);
-    scale_cols(F[b]->V, rs, 0, s.inv, 0, s.Wp, 1, nr, kept, st);
-    scale_cols(F[b]->U, rs, 0, s.inv, 0, s.Zp, 1, nr, kept, st);
+    s.Wp = (double*)E.arena().alloc(sizeof(double) * nr * kb);
+    s.Zp = (double*)E.arena().alloc(sizeof(double) * nr * kb);
+    proj_prepare(F[b]->lam, F[b]->U, F[b]->V, s.inv, s.sinv, 1, nr, rs, kb, h->cut, kRankTol, h->dstatus, st);
+    scale_cols(F[b]->V, rs, 0, s.inv, 0, s.Wp, 1, nr, kb, st);
+    scale_cols(F[b]->U, rs, 0, s.inv, 0, s.Zp, 1, nr, kb, st);
     Tensor P64 = E.zeros(F64, {nl, (int64_t)chi});
     Tensor Q64 = E.zeros(F64, {nl, (int64_t)chi});
     GemmSpec g;
-    g.M = nl; g.N = kept; g.K = nr; g.transA = true; g.lda = nl; g.transB = false; g.ldb = kept; g.ldc = chi;
+    g.M = nl; g.N = kb; g.K = nr; g.transA = true; g.lda = nl; g.transB = false; g.ldb = kb; g.ldc = chi;
     gemm_f64((const double*)S64[b].p, s.Wp, (double*)P64.p, g, st);
     gemm_f64((const double*)N64[b].p, s.Zp, (double*)Q64.p, g, st);
     P64.dims = in[b].pdims;
@@ -569,6 +595,7 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
       if (!gP && !gQ) continue;
       const int64_t nr = inc[b].n_r, nl = inc[b].n_l;
       const int rs = Fc[b].rs;
+      const int kb = std::min(kept, rs);
       auto A64 = [&](int64_t n) { return (double*)E.arena().alloc(sizeof(double) * std::max<int64_t>(n, 1)); };
       double* dP = A64(nl * chi);
       double* dQ = A64(nl * chi);
@@ -581,46 +608,46 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
       const double* lam = Fc[b].lam;
       double* dN = A64(nr * nl);
       double* dS = A64(nr * nl);
-      double* dW = A64(nr * kept);
-      double* dZ = A64(nr * kept);
+      double* dW = A64(nr * kb);
+      double* dZ = A64(nr * kb);
       GemmSpec g;
-      // dS = W dP^t, dN = Z dQ^t  (n_r x n_l, K = kept; dP has leading dimension chi)
-      g.M = nr; g.N = nl; g.K = kept; g.transA = false; g.lda = kept; g.transB = true; g.ldb = chi; g.ldc = nl;
+      // dS = W dP^t, dN = Z dQ^t  (n_r x n_l, K = kb; dP has leading dimension chi)
+      g.M = nr; g.N = nl; g.K = kb; g.transA = false; g.lda = kb; g.transB = true; g.ldb = chi; g.ldc = nl;
       gemm_f64(sv[b].Wp, dP, dS, g, st);
       gemm_f64(sv[b].Zp, dQ, dN, g, st);
-      // dW = S dP, dZ = N dQ (n_r x kept)
+      // dW = S dP, dZ = N dQ (n_r x kb)
       g = GemmSpec();
-      g.M = nr; g.N = kept; g.K = nl; g.transA = false; g.lda = nl; g.transB = false; g.ldb = chi; g.ldc = kept;
+      g.M = nr; g.N = kb; g.K = nl; g.transA = false; g.lda = nl; g.transB = false; g.ldb = chi; g.ldc = kb;
       gemm_f64(S, dP, dW, g, st);
       gemm_f64(N, dQ, dZ, g, st);
-      double* dUk = A64(nr * kept);
-      double* dVk = A64(nr * kept);
-      double* dl = A64(kept);
-      scale_cols(dZ, kept, 0, sv[b].inv, 0, dUk, 1, nr, kept, st);
-      scale_cols(dW, kept, 0, sv[b].inv, 0, dVk, 1, nr, kept, st);
-      proj_dlam(dZ, U, dW, V, sv[b].inv, dl, 1, nr, rs, kept, st);
-      double* Aa = A64((int64_t)rs * kept);
-      double* Bb = A64((int64_t)rs * kept);
+      double* dUk = A64(nr * kb);
+      double* dVk = A64(nr * kb);
+      double* dl = A64(kb);
+      scale_cols(dZ, kb, 0, sv[b].inv, 0, dUk, 1, nr, kb, st);
+      scale_cols(dW, kb, 0, sv[b].inv, 0, dVk, 1, nr, kb, st);
+      proj_dlam(dZ, U, dW, V, sv[b].inv, dl, 1, nr, rs, kb, st);
+      double* Aa = A64((int64_t)rs * kb);
+      double* Bb = A64((int64_t)rs * kb);
       g = GemmSpec();
-      g.M = rs; g.N = kept; g.K = nr; g.transA = true; g.lda = rs; g.transB = false; g.ldb = kept; g.ldc = kept;
+      g.M = rs; g.N = kb; g.K = nr; g.transA = true; g.lda = rs; g.transB = false; g.ldb = kb; g.ldc = kb;
       gemm_f64(U, dUk, Aa, g, st);
       gemm_f64(V, dVk, Bb, g, st);
       double* core = A64((int64_t)rs * rs);
-      proj_core(Aa, Bb, lam, dl, core, 1, rs, kept, kRankTol, eps, st);
-      double* Xu = A64(nr * kept);
-      double* Xv = A64(nr * kept);
+      proj_core(Aa, Bb, lam, dl, core, 1, rs, kb, kRankTol, eps, st);
+      double* Xu = A64(nr * kb);
+      double* Xv = A64(nr * kb);
       g = GemmSpec();
-      g.M = nr; g.N = kept; g.K = rs; g.lda = rs; g.ldb = kept; g.ldc = kept;
+      g.M = nr; g.N = kb; g.K = rs; g.lda = rs; g.ldb = kb; g.ldc = kb;
       gemm_f64(U, Aa, Xu, g, st);
       gemm_f64(V, Bb, Xv, g, st);
-      double* Eu = A64(nr * kept);
-      double* Ev = A64(nr * kept);
-      proj_resid(dUk, Xu, sv[b].sinv, Eu, 1, nr, rs, kept, st);
-      proj_resid(dVk, Xv, sv[b].sinv, Ev, 1, nr, rs, kept, st);
+      double* Eu = A64(nr * kb);
+      double* Ev = A64(nr * kb);
+      proj_resid(dUk, Xu, sv[b].sinv, Eu, 1, nr, rs, kb, st);
+      proj_resid(dVk, Xv, sv[b].sinv, Ev, 1, nr, rs, kb, st);
       // drho = U core V^t + Eu V_k^t + U_k Ev^t is never formed (n_r x n_r); with
       // VtS = V^t S and UtN = U^t N (rs x n_l):
-      //   dN += drho S   = U (core VtS + [Ev^t S; 0]) + Eu VtS[:kept]
-      //   dS += drho^t N = V (core^t UtN + [Eu^t N; 0]) + Ev UtN[:kept]
+      //   dN += drho S   = U (core VtS + [Ev^t S; 0]) + Eu VtS[:kb]
+      //   dS += drho^t N = V (core^t UtN + [Eu^t N; 0]) + Ev UtN[:kb]
       double* VtS = A64((int64_t)rs * nl);
       double* UtN = A64((int64_t)rs * nl);
       g = GemmSpec();
@@ -635,7 +662,7 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
       g.transA = true;
       gemm_f64(core, UtN, G2, g, st);
       g = GemmSpec();
-      g.M = kept; g.N = nl; g.K = nr; g.transA = true; g.lda = kept; g.ldb = nl; g.ldc = nl; g.beta = 1.0;
+      g.M = kb; g.N = nl; g.K = nr; g.transA = true; g.lda = kb; g.ldb = nl; g.ldc = nl; g.beta = 1.0;
       gemm_f64(Ev, S, G1, g, st);
       gemm_f64(Eu, N, G2, g, st);
       g = GemmSpec();
@@ -643,7 +670,7 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
       gemm_f64(U, G1, dN, g, st);
       gemm_f64(V, G2, dS, g, st);
       g = GemmSpec();
-      g.M = nr; g.N = nl; g.K = kept; g.lda = kept; g.ldb = nl; g.ldc = nl; g.beta = 1.0;
+      g.M = nr; g.N = nl; g.K = kb; g.lda = kb; g.ldb = nl; g.ldc = nl; g.beta = 1.0;
       gemm_f64(Eu, VtS, dN, g, st);
       gemm_f64(Ev, UtN, dS, g, st);
       if (inc[b].N.id >= 0) cast(dN, F64, E.grad(inc[b].N), edt, nr * nl, true, st);
@@ -1056,7 +1083,9 @@ int ctm_init(ctm_handle* h, const double* A, const double* env0, void* stream) {
     ctm::ensure_device(h);
     h->eng->set_stream(h->st);
     const int tcm = h->d.precision == CTM_TF32 ? 1 : h->d.precision == CTM_BF16 ? 2 : h->d.precision == CTM_TF32X3 ? 3 : 0;
-    h->eng->set_tc(tcm, h->dstatus);
+    // CTM_TC_MIN_MNK (read at every ctm_init) moves the size threshold of the tensor-core route
+    const char* tmin = getenv("CTM_TC_MIN_MNK");
+    h->eng->set_tc(tcm, h->dstatus, tmin && *tmin ? (int64_t)atoll(tmin) : (int64_t(1) << 26));
     int64_t n = h->A64.numel();
     CTM_CUDA(cudaMemcpyAsync(h->A64.p, A, n * 8, cudaMemcpyDeviceToDevice, h->st));
     if (h->edt != ctm::F64) ctm::cast(h->A64.p, ctm::F64, h->Amode.p, h->edt, n, false, h->st);
@@ -1067,6 +1096,7 @@ int ctm_init(ctm_handle* h, const double* A, const double* env0, void* stream) {
     }
     ctm::load_env(h, h->env0);
     h->iters_done = 0;
+    h->rank_hint.clear();
     h->fac.clear();
     h->ckpt.clear();
     h->store->release({0, 0});
@@ -1114,6 +1144,7 @@ int ctm_grad(ctm_handle* h, int n_iter, double* e_site_dev, double* dA_dev, void
     // forward from the initial environment
     load_env(h, h->env0);
     h->iters_done = 0;
+    h->rank_hint.clear();
     forward_iters(h, n_iter, nullptr);
     const int64_t nA = h->A64.numel();
     CTM_CUDA(cudaMemsetAsync(dA_dev, 0, nA * 8, h->st));
@@ -1230,11 +1261,9 @@ int ctm_profile(ctm_handle* h, int enable) {
   return guard(h, [&]() {
     if (enable) {
       if (h->st || h->dev_ready) CTM_CUDA(cudaStreamSynchronize(h->st));
-      h->prof.used = 0;
-      h->prof.cls.clear();
-      h->prof.flops.clear();
-      h->prof.bytes.clear();
-      for (int c = 0; c < ctm::PROF_NCLASS; ++c) h->prof_ms[c] = h->prof_flops[c] = h->prof_bytes[c] = 0, h->prof_n[c] = 0;
+      h->prof.clear();
+      const char* dump = getenv("CTM_PROF_DUMP");
+      if (dump && *dump && !h->prof.dump) h->prof.dump = fopen(dump, "w");
       ctm::jacobi_flops_read_reset(h->st);
     }
     h->prof.on = enable != 0;
@@ -1246,24 +1275,12 @@ int ctm_profile_read(ctm_handle* h, int cls, double* ms, int64_t* launches, doub
   return guard(h, [&]() {
     CTM_CUDA(cudaStreamSynchronize(h->st));
     auto& P = h->prof;
-    for (size_t k = 0; k + 1 < P.used; k += 2) {
-      float t = 0.f;
-      CTM_CUDA(cudaEventElapsedTime(&t, P.ev[k], P.ev[k + 1]));
-      int c = P.cls[k / 2];
-      h->prof_ms[c] += t;
-      h->prof_n[c] += 1;
-      h->prof_flops[c] += P.flops[k / 2];
-      h->prof_bytes[c] += P.bytes[k / 2];
-    }
-    P.used = 0;
-    P.cls.clear();
-    P.flops.clear();
-    P.bytes.clear();
-    h->prof_flops[ctm::PROF_SVD] += ctm::jacobi_flops_read_reset(h->st);
-    if (ms) *ms = h->prof_ms[cls];
-    if (launches) *launches = h->prof_n[cls];
-    if (flops) *flops = h->prof_flops[cls];
-    if (bytes) *bytes = h->prof_bytes[cls];
+    P.fold();
+    P.fl[ctm::PROF_SVD] += ctm::jacobi_flops_read_reset(h->st);
+    if (ms) *ms = P.ms[cls];
+    if (launches) *launches = P.n[cls];
+    if (flops) *flops = P.fl[cls];
+    if (bytes) *bytes = P.by[cls];
   });
 }
 

@@ -10,11 +10,15 @@
 // contraction is two more contractions (dA = dC . B, dB = A . dC).
 #include "engine.h"
 
+#include <cstdlib>
+
 #include <algorithm>
 #include <cstring>
 #include <numeric>
 
 namespace ctm {
+
+
 
 // ================================================================== Arena
 Arena::~Arena() {
@@ -212,7 +216,11 @@ void Engine::einsum_into(const Tensor& A, const Labels& la, const Tensor& B, con
   const Labels bla = batch;
   // tensor-core route for FP32 contractions: both operands K-major ([batch|M|K] and [batch|N|K])
   const int64_t KK0 = prod(K, dims), MM0 = prod(M, dims), NN0 = prod(N, dims), nb0 = prod(batch, dims);
-  const bool tc = A.dt == F32 && tc_mode_ != 0 && KK0 >= 8 && nb0 <= 65535 && MM0 * NN0 * KK0 >= (int64_t(1) << 15) &&
+  // Small products stay on the CUDA cores: below tc_min_mnk_ multiply-adds (or with an output
+  // side shorter than 32) a tcgen05 tile's fixed cost (TMEM allocation, barrier set-up, pipeline
+  // fill) exceeds the whole FP32 product.
+  const bool tc = A.dt == F32 && tc_mode_ != 0 && KK0 >= 8 && nb0 <= 65535 &&
+                  nb0 * MM0 * NN0 * KK0 >= tc_min_mnk_ && MM0 >= 32 && NN0 >= 32 &&
                   (KK0 * (tc_mode_ == 2 ? 2 : 4)) % 16 == 0;  // modes: 1 tf32, 2 bf16, 3 tf32x3
   if (tc) {
     einsum_tc(A, la, B, lb, lc, out, accumulate, dims, batch, M, N, K, Mlc, Nlc, Klb, nC);

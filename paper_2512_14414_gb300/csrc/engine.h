@@ -91,9 +91,11 @@ class Engine {
 
   // Tensor-core mode of FP32 contractions: 0 SIMT FP32, 1 TF32 (tcgen05 kind::tf32),
   // 2 BF16 operands (tcgen05 kind::f16).  `status` receives device-side error bits.
-  void set_tc(int mode, int* status) {
+  // Products of fewer than min_mnk multiply-adds (batch * M * N * K) stay on the CUDA cores.
+  void set_tc(int mode, int* status, int64_t min_mnk) {
     tc_mode_ = mode;
     tc_status_ = status;
+    tc_min_mnk_ = min_mnk;
   }
   int64_t gemm_flops() const { return gemm_flops_; }
   int64_t perm_bytes() const { return perm_bytes_; }
@@ -110,6 +112,7 @@ class Engine {
   bool record_ = false;
   int tc_mode_ = 0;
   int* tc_status_ = nullptr;
+  int64_t tc_min_mnk_ = int64_t(1) << 26;
   int next_id_ = 0;
   std::vector<std::function<void()>> tape_;
   std::vector<void*> grads_;

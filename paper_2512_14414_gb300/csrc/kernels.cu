@@ -9,21 +9,58 @@ namespace ctm {
 thread_local int64_t* g_launch_counter = nullptr;
 thread_local Profiler* g_prof = nullptr;
 
-void Profiler::begin(int c, cudaStream_t st, double f, double b) {
+void Profiler::begin(int c, cudaStream_t st, double f, double b, const char* tag) {
   if (used + 2 > ev.size()) {
-    if (ev.size() >= (size_t(1) << 20)) return;
-    size_t old = ev.size();
-    ev.resize(std::max<size_t>(4096, ev.size() * 2));
-    for (size_t k = old; k < ev.size(); ++k) cudaEventCreate(&ev[k]);
+    if (ev.size() >= (size_t(1) << 16)) fold();
+    if (used + 2 > ev.size()) {
+      size_t old = ev.size();
+      ev.resize(std::max<size_t>(4096, ev.size() * 2));
+      for (size_t k = old; k < ev.size(); ++k) cudaEventCreate(&ev[k]);
+    }
   }
   cls.push_back(c);
   flops.push_back(f);
   bytes.push_back(b);
+  if (dump) tags.push_back(tag ? tag : "");
   cudaEventRecord(ev[used++], st);
 }
 
 void Profiler::end(cudaStream_t st) {
   if (used % 2 == 1) cudaEventRecord(ev[used++], st);
+}
+
+void Profiler::fold() {
+  if (used == 0) return;
+  cudaEventSynchronize(ev[used - 1]);
+  for (size_t k = 0; k + 1 < used; k += 2) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+    const int c = cls[k / 2];
+    ms[c] += t;
+    n[c] += 1;
+    fl[c] += flops[k / 2];
+    by[c] += bytes[k / 2];
+    if (dump) fprintf(dump, "%d\t%s\t%.6f\n", c, tags[k / 2].c_str(), t);
+  }
+  used = 0;
+  cls.clear();
+  flops.clear();
+  bytes.clear();
+  tags.clear();
+}
+
+void Profiler::clear() {
+  used = 0;
+  cls.clear();
+  flops.clear();
+  bytes.clear();
+  tags.clear();
+  for (int c = 0; c < PROF_NCLASS; ++c) ms[c] = fl[c] = by[c] = 0, n[c] = 0;
+}
+
+Profiler::~Profiler() {
+  for (auto e : ev) cudaEventDestroy(e);
+  if (dump) fclose(dump);
 }
 
 namespace {
@@ -115,7 +152,8 @@ void permute_t(const Ti* in, To* out, const PermSpec& ps, bool acc, double scale
   int64_t n = 1;
   for (int k = 0; k < r; ++k) n *= ps.out_dims[k];
   if (n == 0) return;
-  ProfScope prof(PROF_PERMUTE, st, 0.0, (double)n * (sizeof(Ti) + sizeof(To) * (acc ? 2 : 1)));
+  ProfScope prof(PROF_PERMUTE, st, 0.0, (double)n * (sizeof(Ti) + sizeof(To) * (acc ? 2 : 1)),
+                 prof_tag("permute", ps.rank, n, sizeof(Ti), sizeof(To), acc));
   int64_t ostr[8];
   int64_t s = 1;
   for (int k = r - 1; k >= 0; --k) {
@@ -168,9 +206,11 @@ void permute_t(const Ti* in, To* out, const PermSpec& ps, bool acc, double scale
 // Split-K: with nsplit > 1 the (split, batch) pairs form an extended batch; each block sums its
 // K chunk and writes the raw partial tile to C (a workspace [nsplit][batch][M][N], ldc = N); a
 // second kernel adds the partials in split order (deterministic) and applies alpha and beta.
-template <typename T, int BM, int BN, int BK>
+// 256 threads as a 16 x 16 grid, each owning TM x TN outputs: tiles BM = 16 TM by BN = 16 TN.
+template <typename T, int TM, int TN, int BK>
 __global__ void __launch_bounds__(256) gemm_simt(const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ C,
                                                  GemmSpec g, int64_t nsplit, int64_t kchunk) {
+  constexpr int BM = 16 * TM, BN = 16 * TN;
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -186,11 +226,11 @@ __global__ void __launch_bounds__(256) gemm_simt(const T* __restrict__ A, const 
     const T* Bb = B + bb * g.strideB;
     T* Cb = (nsplit > 1) ? C + ext * g.M * g.N : C + bb * g.strideC;
     const int64_t ldc = (nsplit > 1) ? g.N : g.ldc;
-    T acc[4][4];
+    T acc[TM][TN];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+      for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
     for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
       for (int q = 0; q < (BM * BK) / 256; ++q) {
@@ -227,24 +267,24 @@ __global__ void __launch_bounds__(256) gemm_simt(const T* __restrict__ A, const 
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
-        T a[4], b[4];
+        T a[TM], b[TN];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+        for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+        for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+          for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
       }
       __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < TM; ++i) {
       int64_t m = m0 + ty + 16 * i;
       if (m >= g.M) continue;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < TN; ++j) {
         int64_t n = n0 + tx + 16 * j;
         if (n >= g.N) continue;
         if (nsplit > 1) {
@@ -299,30 +339,43 @@ int num_sms() {
 template <typename T>
 void gemm_t(const T* A, const T* B, T* C, const GemmSpec& g, cudaStream_t st) {
   if (g.M == 0 || g.N == 0 || g.batch == 0) return;
-  ProfScope ps(PROF_GEMM, st, 2.0 * g.batch * g.M * g.N * g.K,
-               (double)sizeof(T) * g.batch * (g.M * g.K + g.K * g.N + (g.beta != 0.0 ? 2 : 1) * g.M * g.N));
+  ProfScope ps(sizeof(T) == 8 ? PROF_GEMM64 : PROF_GEMM, st, 2.0 * g.batch * g.M * g.N * g.K,
+               (double)sizeof(T) * g.batch * (g.M * g.K + g.K * g.N + (g.beta != 0.0 ? 2 : 1) * g.M * g.N),
+               prof_tag(sizeof(T) == 8 ? "simt64" : "simt32", g.batch, g.M, g.N, g.K, g.transA * 2 + g.transB));
   if (g.K == 0) {  // C = beta C
     CTM_CHECK(g.beta == 0.0, CTM_ERR_INVALID_ARG, "gemm with K=0 and beta!=0 unsupported");
     for (int64_t b = 0; b < g.batch; ++b)
       for (int64_t m = 0; m < g.M; ++m) CTM_CUDA(cudaMemsetAsync(C + b * g.strideC + m * g.ldc, 0, g.N * sizeof(T), st));
     return;
   }
-  // split K when the output tiles alone cannot fill the GPU
-  const int64_t tiles = g.batch * ((g.M + 63) / 64) * ((g.N + 63) / 64);
+  // Tile: 64 x 64, or 32 x 32 for FP64 products with a short side (the FP64 pipe is the
+  // bound there, so padded rows cost real time).  K is split when the output tiles alone
+  // cannot fill the GPU: FP64 down to 16-wide chunks, FP32 down to 128-wide chunks (up to
+  // 256 of them for outputs of a few elements with a long K).
+  const bool small = sizeof(T) == 8 && (g.M < 128 || g.N < 128);
+  const int64_t BT = small ? 32 : 64;
+  const int64_t tiles = g.batch * ((g.M + BT - 1) / BT) * ((g.N + BT - 1) / BT);
+  const int64_t min_chunk = sizeof(T) == 8 ? 16 : 128;
+  const int64_t max_split = sizeof(T) == 8 ? 64 : (tiles <= 4 ? 256 : 32);
   int64_t nsplit = 1;
-  if (tiles < 2 * num_sms() && g.K >= 256) {
-    nsplit = std::min<int64_t>({(2 * num_sms() + tiles - 1) / tiles, g.K / 128, 32});
+  if (tiles < 2 * num_sms() && g.K >= 2 * min_chunk) {
+    nsplit = std::min<int64_t>({(2 * num_sms() + tiles - 1) / tiles, g.K / min_chunk, max_split});
+    // workspace bound: 256 MB of partial tiles
+    nsplit = std::min<int64_t>(nsplit, std::max<int64_t>(1, (int64_t(256) << 20) / ((int64_t)sizeof(T) * g.batch * g.M * g.N)));
     if (nsplit < 2) nsplit = 1;
   }
   const int64_t kchunk = ((g.K + nsplit - 1) / nsplit + 15) / 16 * 16;
   nsplit = (g.K + kchunk - 1) / kchunk;
   T* out = C;
   if (nsplit > 1) out = (T*)splitk_workspace(sizeof(T) * nsplit * g.batch * g.M * g.N);
-  const int64_t work = nsplit * g.batch * ((g.M + 63) / 64);
-  CTM_CHECK((g.N + 63) / 64 < (int64_t(1) << 31), CTM_ERR_INVALID_ARG, "gemm N too large");
-  dim3 grid((unsigned)((g.N + 63) / 64), (unsigned)std::min<int64_t>(work, 65535),
+  const int64_t work = nsplit * g.batch * ((g.M + BT - 1) / BT);
+  CTM_CHECK((g.N + BT - 1) / BT < (int64_t(1) << 31), CTM_ERR_INVALID_ARG, "gemm N too large");
+  dim3 grid((unsigned)((g.N + BT - 1) / BT), (unsigned)std::min<int64_t>(work, 65535),
             (unsigned)std::min<int64_t>((work + 65534) / 65535, 65535));
-  gemm_simt<T, 64, 64, 16><<<grid, 256, 0, st>>>(A, B, out, g, nsplit, kchunk);
+  if (small)
+    gemm_simt<T, 2, 2, 16><<<grid, 256, 0, st>>>(A, B, out, g, nsplit, kchunk);
+  else
+    gemm_simt<T, 4, 4, 16><<<grid, 256, 0, st>>>(A, B, out, g, nsplit, kchunk);
   CTM_LAUNCHED();
   if (nsplit > 1) {
     splitk_reduce<T><<<nblocks(g.batch * g.M * g.N, 256), 256, 0, st>>>(out, C, g, nsplit);
@@ -735,7 +788,7 @@ void energy_terms(const double* rho, const double* hs, const double* coup, int n
 
 void split_tf32(const float* x, float* hi, float* lo, int64_t n, cudaStream_t st) {
   if (n == 0) return;
-  ProfScope prof(PROF_PERMUTE, st, 0.0, 12.0 * n);
+  ProfScope prof(PROF_PERMUTE, st, 0.0, 12.0 * n, prof_tag("split_tf32", 1, n, 0, 0));
   split_tf32_k<<<nblocks(n, 256), 256, 0, st>>>(x, hi, lo, n);
   CTM_LAUNCHED();
 }

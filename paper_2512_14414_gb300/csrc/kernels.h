@@ -87,18 +87,16 @@ void qr_apply_Q(const double* A, const double* tau, double* X, int batch, int m,
 void svd_jacobi(double* W, double* V, double* lam, double* Uo, double* Vo, int batch, int r, int max_sweeps,
                 int* status, int* sweeps_out, cudaStream_t st);
 void set_identity_colmajor(double* V, int batch, int r, cudaStream_t st);
-// Truncated SVD of low-numerical-rank r x r matrices (sketch of width l + Jacobi); see linalg.cu.
-void svd_sketch(const double* Wc, int batch, int r, int l, double* lam, double* Uo, double* Vo, int* status,
-                int* sweeps_out, std::vector<int>& incomplete_host, cudaStream_t st);
 // Truncated SVD of rho_b = N_b S_b^t (N_b, S_b: n_r x n_l row-major) without forming rho:
 // Y = N (S^t Omega), Q = orth(Y) (Householder), B^t = S (Q^t N)^t, one-sided Jacobi on the
 // l columns of B^t.  lam: batch x l descending; Uo, Vo: batch x n_r x l row-major with
 // rho ~= U diag(lam) V^t.  ws: svd_sketch_product_ws(...) bytes of device memory.
-// incomplete_host[b] = 1 where the smallest of the l values is above 1e-14 lam_max.
+// incomplete_host[b] = 1 where the smallest of the l values is above 1e-14 lam_max;
+// rank_host[b] = how many of the l values are above 1e-14 lam_max.
 size_t svd_sketch_product_ws(int batch, int nr, int nl, int l);
 void svd_sketch_product(const double* const* N, const double* const* S, int batch, int nr, int nl, int l, double* ws,
                         double* lam, double* Uo, double* Vo, int* status, int* sweeps_out, std::vector<int>& incomplete_host,
-                        cudaStream_t st);
+                        std::vector<int>& rank_host, cudaStream_t st);
 // Flops counted by the Jacobi kernels since the last call (6r per pair test, 12r per rotation).
 double jacobi_flops_read_reset(cudaStream_t st);
 // X[k*m + i] = U[i*r + k] for i < r, 0 for r <= i < m  (k < r): [U; 0] stored column-major.

@@ -458,9 +458,11 @@ __global__ void svd_finalize_kernel(const double* W, const double* V, double* la
 // Finalize of the Jacobi SVD of B^t (m x l, column-major W; V l x l column-major), where
 // B = V W^t.  Sorted descending: lam[rank], Vm (m x ldv row-major, first l columns) = W_k / lam_k,
 // Ul (l x l row-major) = V's column k; flags[b] = 1 when the smallest value is not below
-// 1e-14 lam_max (the sketch may have missed directions).
+// 1e-14 lam_max (the sketch may have missed directions); rank_out[b] = number of values above
+// 1e-14 lam_max.
 __global__ void svd_rect_finalize_kernel(const double* W, const double* V, double* lam, int64_t lam_stride, double* Vm,
-                                         int64_t ldv, double* Ul, int m, int l, int* incomplete, int* status) {
+                                         int64_t ldv, double* Ul, int m, int l, int* incomplete, int* rank_out,
+                                         int* status) {
   extern __shared__ double sm[];
   double* nrm = sm;
   int* rank = (int*)(sm + l);
@@ -492,6 +494,9 @@ __global__ void svd_rect_finalize_kernel(const double* W, const double* V, doubl
       mn = fmin(mn, nrm[k]);
     }
     incomplete[b] = (mn > 1e-14 * mx) ? 1 : 0;
+    int nk = 0;
+    for (int k = 0; k < l; ++k) nk += nrm[k] > 1e-14 * mx;
+    rank_out[b] = nk;
   }
   for (int k = threadIdx.x; k < l; k += blockDim.x) lam[(int64_t)b * lam_stride + rank[k]] = nrm[k];
   for (int64_t e = threadIdx.x; e < (int64_t)m * l; e += blockDim.x) {
@@ -605,7 +610,8 @@ void launch_jacobi(double* W, double* V, int batch, int m, int r, int max_sweeps
 
 void qr_householder(double* A, double* tau, int batch, int m, int n, int64_t strideA, int* status, cudaStream_t st) {
   if (batch == 0 || n == 0) return;
-  ProfScope ps(PROF_QR, st, batch * (2.0 * m * n * n - 2.0 * n * n * n / 3.0), 8.0 * batch * m * n * 2);
+  ProfScope ps(PROF_QR, st, batch * (2.0 * m * n * n - 2.0 * n * n * n / 3.0), 8.0 * batch * m * n * 2,
+               prof_tag("qr", batch, m, n, 0));
   ensure_coop(batch, st);
   const int threads = 256;
   int grid = coop_grid((const void*)qr_kernel, threads);
@@ -626,7 +632,8 @@ void qr_extract_R(const double* A, double* R, int batch, int m, int n, int64_t s
 void qr_apply_Q(const double* A, const double* tau, double* X, int batch, int m, int n, int k, int64_t strideA,
                 int64_t strideX, int* status, cudaStream_t st) {
   if (batch == 0 || n == 0) return;
-  ProfScope ps(PROF_QR, st, batch * 4.0 * m * n * k - 2.0 * batch * n * n * k, 8.0 * batch * (m * n + 2.0 * m * k));
+  ProfScope ps(PROF_QR, st, batch * 4.0 * m * n * k - 2.0 * batch * n * n * k, 8.0 * batch * (m * n + 2.0 * m * k),
+               prof_tag("apply_q", batch, m, n, k));
   ensure_coop(batch, st);
   const int threads = 256;
   int grid = coop_grid((const void*)apply_q_kernel, threads);
@@ -653,87 +660,14 @@ static const double* sketch_omega(int64_t n, cudaStream_t st) {
   return omega;
 }
 
-// Truncated SVD of r x r matrices of low numerical rank by a sketched range finder
-// (Halko, Martinsson & Tropp 2011, Alg. 4.1, Gaussian-like test matrix) followed by the
-// one-sided Jacobi SVD of the l x r projection.  Wc: batch x r x r column-major M (kept).
-// On exit lam (batch x r, descending, zero beyond l), Uo / Vo (batch x r x r row-major,
-// zero beyond column l).  incomplete_host[b] = 1 where the sketch did not reach the
-// rounding floor (1e-14 lam_max): those matrices need the full SVD.
-void svd_sketch(const double* Wc, int batch, int r, int l, double* lam, double* Uo, double* Vo, int* status,
-                int* sweeps_out, std::vector<int>& incomplete_host, cudaStream_t st) {
-  const int64_t rr = (int64_t)r * r, rl = (int64_t)r * l, ll = (int64_t)l * l;
-  static thread_local double* ws = nullptr;
-  static thread_local size_t cap = 0;
-  const size_t need = sizeof(double) * (size_t)batch * (5 * rl + 3 * ll + l) + sizeof(int) * 2 * batch + 4096;
-  if (need > cap) {
-    if (ws) CTM_CUDA(cudaFree(ws));
-    cap = std::max(need, size_t(32) << 20);
-    CTM_CUDA(cudaMalloc(&ws, cap));
-  }
-  const double* omega = sketch_omega(rl, st);
-  double* Y = ws;                       // r x l row-major
-  double* Z = Y + batch * rl;           // r x l row-major
-  double* Yt = Z + batch * rl;          // l x r row-major = Y column-major
-  double* Qc = Yt + batch * rl;         // Q column-major (r x l)
-  double* Bt = Qc + batch * rl;         // B = Q^t M, l x r row-major = B^t column-major
-  double* Vl = Bt + batch * rl;         // l x l Jacobi rotation (column-major)
-  double* Ul = Vl + batch * ll;         // l x l sorted
-  double* tau = Ul + batch * ll;        // l per matrix
-  int* inc = (int*)(tau + batch * l);
-  GemmSpec g;
-  // Y = M Omega (M = Wc^t), stored column-major: Y^t = Omega^t M^t = Omega^t Wc.  No power
-  // iteration: l exceeds the numerical rank (checked below), so range(M Omega) already holds every
-  // direction above the rounding floor, and powers of M would only widen the dynamic range.
-  g = GemmSpec();
-  g.M = l; g.N = r; g.K = r; g.batch = batch; g.transA = true; g.lda = l; g.ldb = r; g.ldc = r;
-  g.strideA = 0; g.strideB = rr; g.strideC = rl;
-  gemm_f64(omega, Wc, Yt, g, st);
-  // orthonormal basis of range(Y): Householder QR, Q formed explicitly
-  qr_householder(Yt, tau, batch, r, l, rl, status, st);
-  eye_rect_kernel<<<dim3((unsigned)std::min<int64_t>(4096, (rl + 255) / 256), batch), 256, 0, st>>>(Qc, r, l);
-  CTM_LAUNCHED();
-  qr_apply_Q(Yt, tau, Qc, batch, r, l, l, rl, rl, status, st);
-  // B^t (column-major r x l) = B row-major (l x r) = Q^t M = Qc^t Wc^t -> row-major: (Qc^t)(Wc^t)
-  g = GemmSpec();
-  g.M = l; g.N = r; g.K = r; g.batch = batch; g.transA = false; g.lda = r; g.transB = true; g.ldb = r; g.ldc = r;
-  g.strideA = rl; g.strideB = rr; g.strideC = rl;
-  gemm_f64(Qc, Wc, Bt, g, st);
-  // one-sided Jacobi on the l columns (length r) of B^t
-  ensure_coop(batch, st);
-  CTM_CUDA(cudaMemsetAsync(g_coop.flags, 0, 3 * batch * sizeof(int), st));
-  CTM_CUDA(cudaMemsetAsync(g_coop.conv, 0, batch * sizeof(int), st));
-  set_identity_colmajor(Vl, batch, l, st);
-  frob2_kernel<<<batch, 256, 0, st>>>(Bt, rl, g_coop.frob2);
-  CTM_LAUNCHED();
-  Sync s{g_coop.bar, g_coop.abort, status};
-  {
-    ProfScope ps(PROF_SVD, st, 0.0, 8.0 * batch * rl * 4);
-    launch_jacobi(Bt, Vl, batch, r, l, 60, g_coop.flags, g_coop.conv, sweeps_out, g_coop.frob2, g_coop.flop_acc, s, st);
-  }
-  CTM_CUDA(cudaMemsetAsync(Uo, 0, sizeof(double) * batch * rr, st));
-  CTM_CUDA(cudaMemsetAsync(Vo, 0, sizeof(double) * batch * rr, st));
-  CTM_CUDA(cudaMemsetAsync(lam, 0, sizeof(double) * batch * r, st));
-  size_t smem = (size_t)l * (sizeof(double) + sizeof(int));
-  svd_rect_finalize_kernel<<<batch, 256, smem, st>>>(Bt, Vl, lam, r, Vo, r, Ul, r, l, inc, status);
-  CTM_LAUNCHED();
-  // U (first l columns of Uo, row-major ld r) = Q Ul
-  g = GemmSpec();
-  g.M = r; g.N = l; g.K = l; g.batch = batch; g.transA = true; g.lda = r; g.ldb = l; g.ldc = r;
-  g.strideA = rl; g.strideB = ll; g.strideC = rr;
-  gemm_f64(Qc, Ul, Uo, g, st);
-  incomplete_host.assign(batch, 0);
-  CTM_CUDA(cudaMemcpyAsync(incomplete_host.data(), inc, sizeof(int) * batch, cudaMemcpyDeviceToHost, st));
-  CTM_CUDA(cudaStreamSynchronize(st));
-}
-
 size_t svd_sketch_product_ws(int batch, int nr, int nl, int l) {
   const size_t per = (size_t)2 * nl * l + (size_t)3 * nr * l + (size_t)2 * l * l + l;
-  return sizeof(double) * batch * per + sizeof(int) * batch + 256;
+  return sizeof(double) * batch * per + sizeof(int) * 2 * batch + 256;
 }
 
 void svd_sketch_product(const double* const* N, const double* const* S, int batch, int nr, int nl, int l, double* ws,
                         double* lam, double* Uo, double* Vo, int* status, int* sweeps_out, std::vector<int>& incomplete_host,
-                        cudaStream_t st) {
+                        std::vector<int>& rank_host, cudaStream_t st) {
   const int64_t Ln = (int64_t)nl * l, Lr = (int64_t)nr * l, ll = (int64_t)l * l;
   const double* omega = sketch_omega(Lr, st);
   double* T = ws;                    // S^t Omega, n_l x l row-major
@@ -778,20 +712,22 @@ void svd_sketch_product(const double* const* N, const double* const* S, int batc
   CTM_LAUNCHED();
   Sync s{g_coop.bar, g_coop.abort, status};
   {
-    ProfScope ps(PROF_SVD, st, 0.0, 8.0 * batch * Lr * 4);
+    ProfScope ps(PROF_SVD, st, 0.0, 8.0 * batch * Lr * 4, prof_tag("jacobi", batch, nr, l, 0));
     launch_jacobi(Bt, Vl, batch, nr, l, 60, g_coop.flags, g_coop.conv, sweeps_out, g_coop.frob2, g_coop.flop_acc, s, st);
   }
   size_t smem = (size_t)l * (sizeof(double) + sizeof(int));
-  svd_rect_finalize_kernel<<<batch, 256, smem, st>>>(Bt, Vl, lam, l, Vo, l, Ul, nr, l, inc, status);
+  svd_rect_finalize_kernel<<<batch, 256, smem, st>>>(Bt, Vl, lam, l, Vo, l, Ul, nr, l, inc, inc + batch, status);
   CTM_LAUNCHED();
   // U = Q Ul (n_r x l row-major)
   g = GemmSpec();
   g.M = nr; g.N = l; g.K = l; g.batch = batch; g.transA = true; g.lda = nr; g.ldb = l; g.ldc = l;
   g.strideA = Lr; g.strideB = ll; g.strideC = Lr;
   gemm_f64(Qc, Ul, Uo, g, st);
-  incomplete_host.assign(batch, 0);
-  CTM_CUDA(cudaMemcpyAsync(incomplete_host.data(), inc, sizeof(int) * batch, cudaMemcpyDeviceToHost, st));
+  std::vector<int> flags(2 * batch, 0);
+  CTM_CUDA(cudaMemcpyAsync(flags.data(), inc, sizeof(int) * 2 * batch, cudaMemcpyDeviceToHost, st));
   CTM_CUDA(cudaStreamSynchronize(st));
+  incomplete_host.assign(flags.begin(), flags.begin() + batch);
+  rank_host.assign(flags.begin() + batch, flags.end());
 }
 
 double jacobi_flops_read_reset(cudaStream_t st) {

@@ -205,7 +205,9 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   ok = __all_sync(0xffffffffu, ok && !*abort_cta);  // tcgen05.ld below is warp-collective
   if (ok) {
-    const int row = m0 + warp * 32 + lane;
+    // Each warp stages its 32 rows x 32 columns through a padded shared buffer (the operand tiles
+    // are no longer read once `done` has fired) so that the global stores run along rows.
+    float* stage = (float*)smem + warp * (32 * 33);
 #pragma unroll 1
     for (int c = 0; c < BN; c += 32) {
       uint32_t v[32];
@@ -219,17 +221,21 @@ __global__ void __launch_bounds__(128, 1)
             "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < M) {
-        float* crow = C + ((int64_t)b * M + row) * (int64_t)N + n0 + c;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          if (n0 + c + j < N) {
-            float x = __uint_as_float(v[j]);
-            if (beta != 0.f) x += beta * crow[j];
-            crow[j] = x;
-          }
+      for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(v[j]);
+      __syncwarp();
+      const int col = n0 + c + lane;
+#pragma unroll 4
+      for (int r = 0; r < 32; ++r) {
+        const int row = m0 + warp * 32 + r;
+        if (row < M && col < N) {
+          float* cp = C + ((int64_t)b * M + row) * (int64_t)N + col;
+          float x = stage[r * 33 + lane];
+          if (beta != 0.f) x += beta * *cp;
+          *cp = x;
         }
       }
+      __syncwarp();
     }
   } else {
     atomicOr(status, DEV_TIMEOUT);
@@ -307,7 +313,8 @@ void gemm_tc(const void* A, const void* B, float* C, int64_t M, int64_t N, int64
   if (M == 0 || N == 0 || batch == 0) return;
   CTM_CHECK(tc_gemm_ok(bf16, M, N, K, A, B), CTM_ERR_INVALID_ARG, "tc gemm: unsupported shape/alignment");
   CTM_CHECK(batch <= 65535, CTM_ERR_INVALID_ARG, "tc gemm: batch too large");
-  ProfScope ps(PROF_TC, st, 2.0 * batch * M * N * K, (double)batch * ((bf16 ? 2 : 4) * (M * K + N * K) + 4.0 * M * N));
+  ProfScope ps(PROF_TC, st, 2.0 * batch * M * N * K, (double)batch * ((bf16 ? 2 : 4) * (M * K + N * K) + 4.0 * M * N),
+               prof_tag(bf16 ? "tc_bf16" : "tc_tf32", batch, M, N, K, beta != 0.0));
   CUtensorMap ma = make_map(A, bf16, M, K, batch), mb = make_map(B, bf16, N, K, batch);
   if (bf16)
     launch_tc<true, false>(ma, mb, ma, mb, C, M, N, batch, K, (float)beta, status, st);
@@ -322,7 +329,8 @@ void gemm_tc_x3(const float* Ahi, const float* Alo, const float* Bhi, const floa
             "tc gemm x3: unsupported shape/alignment");
   CTM_CHECK(batch <= 65535, CTM_ERR_INVALID_ARG, "tc gemm: batch too large");
   // algorithmic flops of the product itself (the three partial products are the compensation)
-  ProfScope ps(PROF_TC, st, 2.0 * batch * M * N * K, (double)batch * (8.0 * (M * K + N * K) + 4.0 * M * N));
+  ProfScope ps(PROF_TC, st, 2.0 * batch * M * N * K, (double)batch * (8.0 * (M * K + N * K) + 4.0 * M * N),
+               prof_tag("tc_x3", batch, M, N, K, beta != 0.0));
   CUtensorMap ma = make_map(Ahi, false, M, K, batch), mb = make_map(Bhi, false, N, K, batch);
   CUtensorMap ma2 = make_map(Alo, false, M, K, batch), mb2 = make_map(Blo, false, N, K, batch);
   launch_tc<false, true>(ma, mb, ma2, mb2, C, M, N, batch, K, (float)beta, status, st);

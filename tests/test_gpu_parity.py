@@ -88,9 +88,14 @@ def test_batched_svd_entry_point():
             assert np.abs(V[k].T @ V[k] - np.eye(r)).max() < 1e-13
 
 
+@pytest.mark.parametrize("tc_min", ["0", None])
 @pytest.mark.parametrize("name,n_iter", [("heis_d2_chi8", 20), ("heis_d4_chi32", 10)])
-def test_mixed_tf32x3_matches_oracle(name, n_iter):
-    # mixed mode: contractions on the tensor cores (error-compensated TF32), decompositions FP64
+def test_mixed_tf32x3_matches_oracle(name, n_iter, tc_min, monkeypatch):
+    # mixed mode: contractions in FP32 -- on the tensor cores (error-compensated TF32) above the size
+    # threshold, which tc_min="0" lowers so that every eligible product takes tcgen05 -- and the
+    # decompositions in FP64
+    if tc_min is not None:
+        monkeypatch.setenv("CTM_TC_MIN_MNK", tc_min)
     w = W.config(name)
     E, g, _ = gpu_energy_grad(w, n_iter, precision="tf32x3")
     Er, gr = oracle_energy_grad(w, n_iter)
@@ -98,8 +103,22 @@ def test_mixed_tf32x3_matches_oracle(name, n_iter):
     assert rel_l2(g, gr) <= 1e-3
 
 
-def test_plain_tf32_and_bf16_run_and_stay_close_in_energy():
+def test_tensor_core_route_runs_when_forced(monkeypatch):
+    # with the threshold at 0 the tcgen05 kernel carries the large contractions of D=4, chi=32
+    monkeypatch.setenv("CTM_TC_MIN_MNK", "0")
+    w = W.config("heis_d4_chi32")
+    ctm = make_ctm(w, "tf32x3")
+    ctm.init(site_stack(w.tensors), env_flat(W.initial_environment(w)))
+    ctm.profile(True)
+    ctm.grad(2)
+    prof = ctm.profile_read()
+    ctm.profile(False)
+    assert prof["tc_gemm"][1] > 0
+
+
+def test_plain_tf32_and_bf16_run_and_stay_close_in_energy(monkeypatch):
     # the uncompensated modes are faster but coarser: their energy is reported, not held to 1e-6
+    monkeypatch.setenv("CTM_TC_MIN_MNK", "0")
     w = W.config("heis_d2_chi8")
     Er, _ = oracle_energy_grad(w, w.n_iter, grad=False)
     for prec, tol in (("tf32", 1e-3), ("bf16", 1e-2)):

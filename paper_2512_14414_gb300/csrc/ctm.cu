@@ -131,6 +131,11 @@ struct ctm_handle {
   };
   std::vector<std::vector<Fac>> fac;  // [iteration][projector pair]
   std::vector<int> rank_hint;         // [projector pair] numerical rank of rho in the previous iteration (0: unknown)
+  // Side streams for the independent rows of a column step (fork from / join into st).
+  static constexpr int kRowStreams = 4;
+  cudaStream_t row_st[kRowStreams] = {};
+  cudaEvent_t row_ev[kRowStreams] = {};
+  cudaEvent_t fork_ev = nullptr;
   int iters_done = 0;
   int* dstatus = nullptr;
   int* dsweeps = nullptr;
@@ -493,6 +498,22 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
       l = known ? std::min(r, std::max(16, (hmax + 12 + 7) / 8 * 8)) : std::min(r, std::max(chi + 16, 32));
       std::vector<const double*> Np(ng), Sp(ng);
       for (int g = 0; g < ng; ++g) Np[g] = (const double*)N64[grp[g]].p, Sp[g] = (const double*)S64[grp[g]].p;
+      // warm start from the same pair's right singular vectors of the previous iteration
+      std::vector<const double*> Wp(ng, nullptr);
+      int kw = 0, ldw = 0;
+      if (known && h->cur_iter > 0 && (int)h->fac[h->cur_iter - 1].size() >= h->cur_pair + nb) {
+        auto& prev = h->fac[h->cur_iter - 1];
+        bool same = true;
+        for (int g = 0; g < ng; ++g) {
+          const ctm_handle::Fac& f = prev[h->cur_pair + grp[g]];
+          same = same && f.V && f.n_r == nr && f.rs == prev[h->cur_pair + grp[0]].rs;
+        }
+        if (same) {
+          ldw = prev[h->cur_pair + grp[0]].rs;
+          kw = std::min(hmax, ldw);
+          for (int g = 0; g < ng; ++g) Wp[g] = prev[h->cur_pair + grp[g]].V;
+        }
+      }
       bool ok = false;
       for (int attempt = 0; attempt < 2 && !ok && 2 * l <= r; ++attempt) {
         double* ws = (double*)E.arena().alloc(svd_sketch_product_ws(ng, nr, nl, l));
@@ -500,7 +521,9 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
         double* Uo = (double*)E.arena().alloc(sizeof(double) * ng * (int64_t)nr * l);
         double* Vo = (double*)E.arena().alloc(sizeof(double) * ng * (int64_t)nr * l);
         std::vector<int> inc, rk;
-        svd_sketch_product(Np.data(), Sp.data(), ng, nr, nl, l, ws, lam, Uo, Vo, h->dstatus, h->dsweeps, inc, rk, st);
+        const int kwa = std::min(kw, l - 8);
+        svd_sketch_product(Np.data(), Sp.data(), ng, nr, nl, l, kwa > 0 ? Wp.data() : nullptr, ldw, std::max(kwa, 0), ws,
+                           lam, Uo, Vo, h->dstatus, h->dsweeps, inc, rk, st);
         ok = true;
         for (int x : inc) ok = ok && x == 0;
         if (!ok) {
@@ -679,6 +702,41 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
   });
 }
 
+// ------------------------------------------------------------------ row streams
+// The rows of one column step contract independent networks: each runs on its own side stream,
+// forked from the main stream (side streams wait for all work enqueued so far) and joined back
+// (the main stream waits for all of them) before anything reads their results.  While forked,
+// the engine keeps the temporaries of each contraction (the arena is shared by the streams);
+// they are recycled with the column step.  CTM_ROW_STREAMS=0 keeps every row on the main stream.
+static bool row_streams_on() {
+  static const bool on = []() {
+    const char* e = getenv("CTM_ROW_STREAMS");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+void fork_rows(ctm_handle* h) {
+  if (!row_streams_on()) return;
+  CTM_CUDA(cudaEventRecord(h->fork_ev, h->st));
+  for (int k = 0; k < ctm_handle::kRowStreams; ++k) CTM_CUDA(cudaStreamWaitEvent(h->row_st[k], h->fork_ev, 0));
+  h->eng->set_defer_release(true);
+}
+
+void use_row_stream(ctm_handle* h, int i) {
+  if (row_streams_on()) h->eng->set_stream(h->row_st[i % ctm_handle::kRowStreams]);
+}
+
+void join_rows(ctm_handle* h) {
+  if (!row_streams_on()) return;
+  for (int k = 0; k < ctm_handle::kRowStreams; ++k) {
+    CTM_CUDA(cudaEventRecord(h->row_ev[k], h->row_st[k]));
+    CTM_CUDA(cudaStreamWaitEvent(h->st, h->row_ev[k], 0));
+  }
+  h->eng->set_stream(h->st);
+  h->eng->set_defer_release(false);
+}
+
 // ------------------------------------------------------------------ one left move (in frame q)
 void left_move(ctm_handle* h, int q) {
   Engine& E = *h->eng;
@@ -687,7 +745,9 @@ void left_move(ctm_handle* h, int q) {
   for (int j = 0; j < F.FC; ++j) {
     auto mark = h->tape->mark();
     std::vector<PairIn> pin(F.FR);
+    fork_rows(h);
     for (int i = 0; i < F.FR; ++i) {
+      use_row_stream(h, i);
       Net net;
       int s00 = F.site(i, j), s01 = F.site(i, j + 1), s10 = F.site(i + 1, j), s11 = F.site(i + 1, j + 1);
       Pos p00 = make_pos(h, net, s00, q, false), p01 = make_pos(h, net, s01, q, false);
@@ -736,11 +796,14 @@ void left_move(ctm_handle* h, int q) {
       for (int x : lcutS) pi.qdims.push_back(net.dim[x]);
       pi.qdims.push_back(chi);
     }
+    join_rows(h);
     std::vector<Tensor> P, Q;
     projectors(h, pin, P, Q);
     // absorb column j into the left environment of column j + 1
     std::vector<std::array<Tensor, 3>> nw(F.FR);
+    fork_rows(h);
     for (int i = 0; i < F.FR; ++i) {
+      use_row_stream(h, i);
       const int im = mod(i - 1, F.FR);
       const int s = F.site(i, j);
       Net net;
@@ -775,6 +838,7 @@ void left_move(ctm_handle* h, int q) {
         nw[i][2] = E.normalize(contract_greedy(E, net, v, &o).t);
       }
     }
+    join_rows(h);
     for (int i = 0; i < F.FR; ++i) {
       const int t = F.site(i, j + 1);
       const int ks[3] = {F.slot(S_CUL), F.slot(S_TL), F.slot(S_CDL)};
@@ -884,6 +948,11 @@ void energy_op(ctm_handle* h, double* e_site, double* e_bonds, bool backward_see
 // ------------------------------------------------------------------ device state
 void ensure_device(ctm_handle* h) {
   if (h->dev_ready) return;
+  for (int k = 0; k < ctm_handle::kRowStreams; ++k) {
+    CTM_CUDA(cudaStreamCreateWithFlags(&h->row_st[k], cudaStreamNonBlocking));
+    CTM_CUDA(cudaEventCreateWithFlags(&h->row_ev[k], cudaEventDisableTiming));
+  }
+  CTM_CUDA(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
   h->persist.reset(new Arena(size_t(64) << 20));
   h->tape.reset(new Arena(size_t(256) << 20));
   h->store.reset(new Arena(size_t(256) << 20));
@@ -1321,6 +1390,14 @@ int ctm_svd(const double* M, int batch, int r, double* U, double* s, double* V, 
 
 int ctm_destroy(ctm_handle* h) {
   if (!h) return CTM_ERR_INVALID_ARG;
+  for (int k = 0; k < ctm_handle::kRowStreams; ++k) {
+    if (h->row_st[k]) {
+      cudaStreamSynchronize(h->row_st[k]);
+      cudaStreamDestroy(h->row_st[k]);
+    }
+    if (h->row_ev[k]) cudaEventDestroy(h->row_ev[k]);
+  }
+  if (h->fork_ev) cudaEventDestroy(h->fork_ev);
   h->eng.reset();
   h->persist.reset();
   h->tape.reset();

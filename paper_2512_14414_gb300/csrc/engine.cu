@@ -310,8 +310,9 @@ void Engine::einsum_into(const Tensor& A, const Labels& la, const Tensor& B, con
     ctm::permute(Cp, A.dt, out, A.dt, perm_spec(nat, lc, dims), accumulate, 1.0, st_);
     perm_bytes_ += (accumulate ? 3 : 2) * nC * es;
   }
-  // temporaries are dead once the kernels above are enqueued in stream order
-  arena_->release(mark);
+  // temporaries are dead once the kernels above are enqueued in stream order (not while several
+  // streams draw on the arena: then the next contraction may run concurrently on another stream)
+  if (!defer_release_) arena_->release(mark);
 }
 
 void Engine::einsum_tc(const Tensor& A, const Labels& la, const Tensor& B, const Labels& lb, const Labels& lc,
@@ -380,7 +381,7 @@ void Engine::einsum_tc(const Tensor& A, const Labels& la, const Tensor& B, const
     ctm::permute(Cp, F32, out, F32, perm_spec(nat, lc, dims), accumulate, 1.0, st_);
     perm_bytes_ += (accumulate ? 3 : 2) * nC * 4;
   }
-  arena_->release(mark);
+  if (!defer_release_) arena_->release(mark);
 }
 
 Tensor Engine::einsum(const Tensor& A, const Labels& la, const Tensor& B, const Labels& lb, const Labels& lc) {

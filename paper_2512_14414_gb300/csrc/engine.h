@@ -54,6 +54,9 @@ class Engine {
   Engine(cudaStream_t st, Arena* arena) : st_(st), arena_(arena) {}
   cudaStream_t stream() const { return st_; }
   void set_stream(cudaStream_t s) { st_ = s; }
+  // While on, contractions keep their temporaries (the caller releases them later): set when
+  // work is spread over several streams that share the arena.
+  void set_defer_release(bool on) { defer_release_ = on; }
   Arena& arena() { return *arena_; }
 
   Tensor empty(DType dt, const std::vector<int64_t>& dims);
@@ -113,6 +116,7 @@ class Engine {
   int tc_mode_ = 0;
   int* tc_status_ = nullptr;
   int64_t tc_min_mnk_ = int64_t(1) << 26;
+  bool defer_release_ = false;
   int next_id_ = 0;
   std::vector<std::function<void()>> tape_;
   std::vector<void*> grads_;

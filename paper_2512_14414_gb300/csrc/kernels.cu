@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
 
 namespace ctm {
 
@@ -313,17 +314,25 @@ __global__ void splitk_reduce(const T* __restrict__ W, T* __restrict__ C, GemmSp
   }
 }
 
-// per-thread cached workspace of the split-K partial tiles
-thread_local void* g_splitk_ws = nullptr;
-thread_local size_t g_splitk_cap = 0;
+// Cached workspace of the split-K partial tiles, one per (host thread, stream): products
+// enqueued on different streams may run at the same time.
+struct SplitkWs {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+thread_local std::map<cudaStream_t, SplitkWs> g_splitk_ws;
 
-void* splitk_workspace(size_t bytes) {
-  if (bytes > g_splitk_cap) {
-    if (g_splitk_ws) CTM_CUDA(cudaFree(g_splitk_ws));
-    g_splitk_cap = std::max(bytes, size_t(64) << 20);
-    CTM_CUDA(cudaMalloc(&g_splitk_ws, g_splitk_cap));
+void* splitk_workspace(size_t bytes, cudaStream_t st) {
+  SplitkWs& w = g_splitk_ws[st];
+  if (bytes > w.cap) {
+    if (w.p) {  // launches already enqueued on st may still read the old buffer
+      CTM_CUDA(cudaStreamSynchronize(st));
+      CTM_CUDA(cudaFree(w.p));
+    }
+    w.cap = std::max(bytes, size_t(64) << 20);
+    CTM_CUDA(cudaMalloc(&w.p, w.cap));
   }
-  return g_splitk_ws;
+  return w.p;
 }
 
 int num_sms() {
@@ -349,10 +358,13 @@ void gemm_t(const T* A, const T* B, T* C, const GemmSpec& g, cudaStream_t st) {
     return;
   }
   // Tile: 64 x 64, or 32 x 32 for FP64 products with a short side (the FP64 pipe is the
-  // bound there, so padded rows cost real time).  K is split when the output tiles alone
+  // bound there, so padded rows cost real time) and for FP32 products whose 64 x 64 tiles would
+  // not cover the SMs.  K is split when the output tiles alone
   // cannot fill the GPU: FP64 down to 16-wide chunks, FP32 down to 128-wide chunks (up to
   // 256 of them for outputs of a few elements with a long K).
-  const bool small = sizeof(T) == 8 && (g.M < 128 || g.N < 128);
+  const bool small = sizeof(T) == 8 ? (g.M < 128 || g.N < 128)
+                                     : (g.M < 64 || g.N < 64 ||
+                                        g.batch * ((g.M + 63) / 64) * ((g.N + 63) / 64) < num_sms());
   const int64_t BT = small ? 32 : 64;
   const int64_t tiles = g.batch * ((g.M + BT - 1) / BT) * ((g.N + BT - 1) / BT);
   const int64_t min_chunk = sizeof(T) == 8 ? 16 : 128;
@@ -367,7 +379,7 @@ void gemm_t(const T* A, const T* B, T* C, const GemmSpec& g, cudaStream_t st) {
   const int64_t kchunk = ((g.K + nsplit - 1) / nsplit + 15) / 16 * 16;
   nsplit = (g.K + kchunk - 1) / kchunk;
   T* out = C;
-  if (nsplit > 1) out = (T*)splitk_workspace(sizeof(T) * nsplit * g.batch * g.M * g.N);
+  if (nsplit > 1) out = (T*)splitk_workspace(sizeof(T) * nsplit * g.batch * g.M * g.N, st);
   const int64_t work = nsplit * g.batch * ((g.M + BT - 1) / BT);
   CTM_CHECK((g.N + BT - 1) / BT < (int64_t(1) << 31), CTM_ERR_INVALID_ARG, "gemm N too large");
   dim3 grid((unsigned)((g.N + BT - 1) / BT), (unsigned)std::min<int64_t>(work, 65535),

@@ -94,9 +94,13 @@ void set_identity_colmajor(double* V, int batch, int r, cudaStream_t st);
 // incomplete_host[b] = 1 where the smallest of the l values is above 1e-14 lam_max;
 // rank_host[b] = how many of the l values are above 1e-14 lam_max.
 size_t svd_sketch_product_ws(int batch, int nr, int nl, int l);
-void svd_sketch_product(const double* const* N, const double* const* S, int batch, int nr, int nl, int l, double* ws,
-                        double* lam, double* Uo, double* Vo, int* status, int* sweeps_out, std::vector<int>& incomplete_host,
-                        std::vector<int>& rank_host, cudaStream_t st);
+// warm (nullable): per matrix an n_r x kw block (row-major, ld ldw) that replaces the first kw
+// columns of the random test matrix -- the previous right singular vectors, so that rho Omega
+// is already close to U Sigma and the Jacobi sweeps start near convergence.
+void svd_sketch_product(const double* const* N, const double* const* S, int batch, int nr, int nl, int l,
+                        const double* const* warm, int ldw, int kw, double* ws, double* lam, double* Uo, double* Vo,
+                        int* status, int* sweeps_out, std::vector<int>& incomplete_host, std::vector<int>& rank_host,
+                        cudaStream_t st);
 // Flops counted by the Jacobi kernels since the last call (6r per pair test, 12r per rotation).
 double jacobi_flops_read_reset(cudaStream_t st);
 // X[k*m + i] = U[i*r + k] for i < r, 0 for r <= i < m  (k < r): [U; 0] stored column-major.

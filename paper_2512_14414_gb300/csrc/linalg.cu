@@ -58,7 +58,7 @@ __device__ bool grid_barrier(const Sync& s) {
           ok = 0;
           break;
         }
-        if (spins > 64) __nanosleep(256);
+        if (spins > 64) __nanosleep(32);
       }
     }
     __threadfence();
@@ -665,9 +665,10 @@ size_t svd_sketch_product_ws(int batch, int nr, int nl, int l) {
   return sizeof(double) * batch * per + sizeof(int) * 2 * batch + 256;
 }
 
-void svd_sketch_product(const double* const* N, const double* const* S, int batch, int nr, int nl, int l, double* ws,
-                        double* lam, double* Uo, double* Vo, int* status, int* sweeps_out, std::vector<int>& incomplete_host,
-                        std::vector<int>& rank_host, cudaStream_t st) {
+void svd_sketch_product(const double* const* N, const double* const* S, int batch, int nr, int nl, int l,
+                        const double* const* warm, int ldw, int kw, double* ws, double* lam, double* Uo, double* Vo,
+                        int* status, int* sweeps_out, std::vector<int>& incomplete_host, std::vector<int>& rank_host,
+                        cudaStream_t st) {
   const int64_t Ln = (int64_t)nl * l, Lr = (int64_t)nr * l, ll = (int64_t)l * l;
   const double* omega = sketch_omega(Lr, st);
   double* T = ws;                    // S^t Omega, n_l x l row-major
@@ -680,11 +681,17 @@ void svd_sketch_product(const double* const* N, const double* const* S, int batc
   double* tau = Ul + batch * ll;     // l per matrix
   int* inc = (int*)(tau + batch * l);
   GemmSpec g;
+  if (!warm) kw = 0;
   for (int b = 0; b < batch; ++b) {
-    // T = S^t Omega
+    // T = S^t Omega, Omega = [warm_b(:, :kw) | random columns]
+    if (kw > 0) {
+      g = GemmSpec();
+      g.M = nl; g.N = kw; g.K = nr; g.transA = true; g.lda = nl; g.ldb = ldw; g.ldc = l;
+      gemm_f64(S[b], warm[b], T + b * Ln, g, st);
+    }
     g = GemmSpec();
-    g.M = nl; g.N = l; g.K = nr; g.transA = true; g.lda = nl; g.ldb = l; g.ldc = l;
-    gemm_f64(S[b], omega, T + b * Ln, g, st);
+    g.M = nl; g.N = l - kw; g.K = nr; g.transA = true; g.lda = nl; g.ldb = l; g.ldc = l;
+    gemm_f64(S[b], omega + kw, T + b * Ln + kw, g, st);
     // Y^t = T^t N^t
     g = GemmSpec();
     g.M = l; g.N = nr; g.K = nl; g.transA = true; g.lda = l; g.transB = true; g.ldb = nl; g.ldc = nr;

@@ -211,6 +211,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true", help="skip the nvidia-smi clock sampler (profiler runs)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 reference evaluation of the same workload")
     args = ap.parse_args()
 
     import workloads as W
@@ -255,7 +256,6 @@ def main():
     clocks = Clocks(local, enabled=not args.no_clocks)
     clocks.start()
     launches0 = ctm.kernel_launches
-    ctm.profile(True)
     st = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -267,9 +267,19 @@ def main():
     if world > 1:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
+    launches = ctm.kernel_launches - launches0
+    # One more step of the same workload with a CUDA-event pair around every launch (on the stream
+    # each kernel is launched on): per-class device time, launch counts and algorithmic work for
+    # the roofline.  Kept out of the K timed steps because the events themselves cost ~15%.
+    ctm.profile(True)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(st)
+    step()
+    p1.record(st)
     prof = ctm.profile_read()
     ctm.profile(False)
-    launches = ctm.kernel_launches - launches0
+    torch.cuda.synchronize()
+    profiled_ms = p0.elapsed_time(p1)
     ck = clocks.stop()
     t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
     if world > 1:
@@ -302,12 +312,38 @@ def main():
                "h2d_bytes_per_step": int(Ap.numel() * 8 + Ep.numel() * 8),
                "d2h_bytes_per_step": int(dA_h.numel() * 8 + 8)}
 
+    # the same evaluation in FP64 (the accuracy reference of the mixed modes): 1 warm-up, 1 timed
+    fp64 = None
+    if not args.no_fp64 and args.precision != "fp64" and rank == 0:
+        ctm64 = CTM(w.Lx, w.Ly, w.d, w.D, w.chi, [(t.x, t.y, t.kind, t.coupling, t.h) for t in w.terms],
+                    precision="fp64")
+        e64 = torch.empty(1, dtype=torch.float64, device=dev)
+        dA64 = torch.empty_like(A)
+        ctm64.init(A, E0)
+        ctm64.grad(w.n_iter, dA=dA64, e=e64)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(st)
+        ctm64.init(A, E0)
+        ctm64.grad(w.n_iter, dA=dA64, e=e64)
+        f1.record(st)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        E64 = float(e64[0])
+        grel = float((dA - dA64).norm() / dA64.norm())
+        fp64 = {"value": 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64, "energy": E64,
+                "abs_dE_mixed_vs_fp64": abs(E_val - E64), "grad_rel_l2_mixed_vs_fp64": grel,
+                "speedup_mixed_over_fp64": ms64 / (ms_max / args.steps)}
+        del ctm64
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
     peaks, kind = _peaks()
     roof = _roofline(prof, args.precision, peaks, kind)
+    if roof is not None:
+        roof["measured_on"] = f"one profiled step after the timed region ({profiled_ms:.0f} ms with events)"
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = _cpu_baseline(w, os.cpu_count() or 1)
@@ -322,6 +358,7 @@ def main():
                    "n_iter": w.n_iter, "precision": args.precision, "parallelism": f"replicas x{world}",
                    "l2": "per-step working set (checkpoints, projector factors, tape) is several GB > 129 MB L2"},
         "energy": E_val,
+        "fp64": fp64,
         "roofline": roof,
         "kernel_time_share": {k: round(v[0] / total_ms, 4) for k, v in prof.items() if v[1]},
         "cpu_baseline": cpu,

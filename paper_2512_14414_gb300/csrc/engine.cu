@@ -218,9 +218,12 @@ void Engine::einsum_into(const Tensor& A, const Labels& la, const Tensor& B, con
   const int64_t KK0 = prod(K, dims), MM0 = prod(M, dims), NN0 = prod(N, dims), nb0 = prod(batch, dims);
   // Small products stay on the CUDA cores: below tc_min_mnk_ multiply-adds (or with an output
   // side shorter than 32) a tcgen05 tile's fixed cost (TMEM allocation, barrier set-up, pipeline
-  // fill) exceeds the whole FP32 product.
+  // fill) exceeds the whole FP32 product, and with fewer than 8 output tiles a long K runs on a
+  // handful of SMs where the CUDA-core path splits it.
+  const int64_t tiles0 = nb0 * ((MM0 + 127) / 128) * ((NN0 + 127) / 128);
   const bool tc = A.dt == F32 && tc_mode_ != 0 && KK0 >= 8 && nb0 <= 65535 &&
                   nb0 * MM0 * NN0 * KK0 >= tc_min_mnk_ && MM0 >= 32 && NN0 >= 32 &&
+                  (tiles0 >= 8 || tc_min_mnk_ == 0) &&
                   (KK0 * (tc_mode_ == 2 ? 2 : 4)) % 16 == 0;  // modes: 1 tf32, 2 bf16, 3 tf32x3
   if (tc) {
     einsum_tc(A, la, B, lb, lc, out, accumulate, dims, batch, M, N, K, Mlc, Nlc, Klb, nC);

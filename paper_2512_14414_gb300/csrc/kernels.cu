@@ -208,12 +208,15 @@ void permute_t(const Ti* in, To* out, const PermSpec& ps, bool acc, double scale
 // K chunk and writes the raw partial tile to C (a workspace [nsplit][batch][M][N], ldc = N); a
 // second kernel adds the partials in split order (deterministic) and applies alpha and beta.
 // 256 threads as a 16 x 16 grid, each owning TM x TN outputs: tiles BM = 16 TM by BN = 16 TN.
+// Shared memory is double-buffered and the next K tile is fetched into registers while the
+// current one is multiplied, so one global-load latency is hidden per K step.
 template <typename T, int TM, int TN, int BK>
 __global__ void __launch_bounds__(256) gemm_simt(const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ C,
                                                  GemmSpec g, int64_t nsplit, int64_t kchunk) {
   constexpr int BM = 16 * TM, BN = 16 * TN;
-  __shared__ T As[BK][BM + 1];
-  __shared__ T Bs[BK][BN + 1];
+  constexpr int LA = (BM * BK) / 256, LB = (BN * BK) / 256;
+  __shared__ T As[2][BK][BM + 1];
+  __shared__ T Bs[2][BK][BN + 1];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int64_t n0 = (int64_t)blockIdx.x * BN;
   const int64_t mtiles = (g.M + BM - 1) / BM;
@@ -227,58 +230,67 @@ __global__ void __launch_bounds__(256) gemm_simt(const T* __restrict__ A, const 
     const T* Bb = B + bb * g.strideB;
     T* Cb = (nsplit > 1) ? C + ext * g.M * g.N : C + bb * g.strideC;
     const int64_t ldc = (nsplit > 1) ? g.N : g.ldc;
+    T ra[LA], rb[LB];
+    // global -> registers for the K tile starting at k0
+    auto fetch = [&](int64_t k0) {
+#pragma unroll
+      for (int q = 0; q < LA; ++q) {
+        const int e = threadIdx.x + 256 * q;
+        const int ml = g.transA ? e % BM : e / BK, kl = g.transA ? e / BM : e % BK;
+        const int64_t m = m0 + ml, k = k0 + kl;
+        ra[q] = (m < g.M && k < kend) ? (g.transA ? Ab[k * g.lda + m] : Ab[m * g.lda + k]) : T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < LB; ++q) {
+        const int e = threadIdx.x + 256 * q;
+        const int nl = g.transB ? e / BK : e % BN, kl = g.transB ? e % BK : e / BN;
+        const int64_t n = n0 + nl, k = k0 + kl;
+        rb[q] = (n < g.N && k < kend) ? (g.transB ? Bb[n * g.ldb + k] : Bb[k * g.ldb + n]) : T(0);
+      }
+    };
+    // registers -> shared buffer `buf`
+    auto stash = [&](int buf) {
+#pragma unroll
+      for (int q = 0; q < LA; ++q) {
+        const int e = threadIdx.x + 256 * q;
+        const int ml = g.transA ? e % BM : e / BK, kl = g.transA ? e / BM : e % BK;
+        As[buf][kl][ml] = ra[q];
+      }
+#pragma unroll
+      for (int q = 0; q < LB; ++q) {
+        const int e = threadIdx.x + 256 * q;
+        const int nl = g.transB ? e / BK : e % BN, kl = g.transB ? e % BK : e / BN;
+        Bs[buf][kl][nl] = rb[q];
+      }
+    };
     T acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
       for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+    __syncthreads();  // the previous work item may still read both buffers
+    fetch(kbeg);
+    stash(0);
+    __syncthreads();
+    int buf = 0;
     for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
-#pragma unroll
-      for (int q = 0; q < (BM * BK) / 256; ++q) {
-        int e = threadIdx.x + 256 * q;
-        int ml, kl;
-        if (g.transA) {
-          ml = e % BM;
-          kl = e / BM;
-        } else {
-          kl = e % BK;
-          ml = e / BK;
-        }
-        int64_t m = m0 + ml, k = k0 + kl;
-        T v = T(0);
-        if (m < g.M && k < kend) v = g.transA ? Ab[k * g.lda + m] : Ab[m * g.lda + k];
-        As[kl][ml] = v;
-      }
-#pragma unroll
-      for (int q = 0; q < (BN * BK) / 256; ++q) {
-        int e = threadIdx.x + 256 * q;
-        int nl, kl;
-        if (g.transB) {
-          kl = e % BK;
-          nl = e / BK;
-        } else {
-          nl = e % BN;
-          kl = e / BN;
-        }
-        int64_t n = n0 + nl, k = k0 + kl;
-        T v = T(0);
-        if (n < g.N && k < kend) v = g.transB ? Bb[n * g.ldb + k] : Bb[k * g.ldb + n];
-        Bs[kl][nl] = v;
-      }
-      __syncthreads();
+      const bool more = k0 + BK < kend;
+      if (more) fetch(k0 + BK);
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
         T a[TM], b[TN];
 #pragma unroll
-        for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
+        for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty + 16 * i];
 #pragma unroll
-        for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + 16 * j];
+        for (int j = 0; j < TN; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
           for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
       }
+      if (more) stash(buf ^ 1);
       __syncthreads();
+      buf ^= 1;
     }
 #pragma unroll
     for (int i = 0; i < TM; ++i) {

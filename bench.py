@@ -281,10 +281,8 @@ def main():
     torch.cuda.synchronize()
     profiled_ms = p0.elapsed_time(p1)
     ck = clocks.stop()
-    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_max = float(t_max[0])
+    from paper_2512_14414_gb300.replicas import max_over_ranks
+    ms_max = max_over_ranks(ms)
     value = world * args.steps / (ms_max * 1e-3)
     E_val = float(e[0])
 
@@ -304,11 +302,8 @@ def main():
             dA_h.copy_(dA, non_blocking=True)
             e_h.copy_(e, non_blocking=True)
             torch.cuda.synchronize()
-        te = time.perf_counter() - t
-        tt = torch.tensor([te], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * args.steps / float(tt[0]), "unit": UNIT,
+        te = max_over_ranks(time.perf_counter() - t)
+        e2e = {"value": world * args.steps / te, "unit": UNIT,
                "h2d_bytes_per_step": int(Ap.numel() * 8 + Ep.numel() * 8),
                "d2h_bytes_per_step": int(dA_h.numel() * 8 + 8)}
 

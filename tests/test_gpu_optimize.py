@@ -1,0 +1,61 @@
+"""GPU gradient against finite differences, and the L-BFGS loop on the GPU against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from gpu_helpers import env_flat, make_ctm, site_stack
+
+pytestmark = pytest.mark.gpu
+
+
+def test_gradient_matches_central_finite_differences_on_64_entries():
+    # D=4, chi=32 (fewer iterations than the 40 of that workload to keep the test short):
+    # dE/dA from the reverse mode vs (E(A + h e_k) - E(A - h e_k)) / 2h, h = 1e-6, on 64 entries
+    # drawn with seed 1001; both sides evaluate the same function (same env0 and iterations)
+    w = W.config("heis_d4_chi32")
+    n_iter = 12
+    ctm = make_ctm(w, "fp64")
+    A = site_stack(w.tensors)
+    env0 = env_flat(W.initial_environment(w))
+    ctm.init(A, env0)
+    _, dA = ctm.grad(n_iter)
+    g = dA.cpu().numpy().ravel()
+    idx = np.random.default_rng(1001).choice(A.numel(), size=64, replace=False)
+    h = 1e-6
+
+    def energy(x):
+        ctm.init(x, env0)
+        ctm.step(n_iter)
+        return float(ctm.energy()[0])
+
+    fd = []
+    for k in idx:
+        Ap = A.clone().view(-1)
+        Ap[k] += h
+        Am = A.clone().view(-1)
+        Am[k] -= h
+        fd.append((energy(Ap.view_as(A)) - energy(Am.view_as(A))) / (2 * h))
+    fd = np.array(fd)
+    scale = np.abs(g).max()
+    assert np.abs(g[idx] - fd).max() <= 1e-6 * scale + 1e-9, np.abs(g[idx] - fd).max() / scale
+
+
+def test_lbfgs_on_the_gpu_follows_the_oracle_trajectory():
+    from oracle.api import evaluate
+    from paper_2512_14414_gb300.lbfgs import lbfgs, optimize_peps
+    w = W.config("heis_d2_chi8")
+    n_iter = 10
+    env0_h = W.initial_environment(w)
+    A0 = np.stack(w.tensors)
+    ctm = make_ctm(w, "fp64")
+    gpu = optimize_peps(ctm, A0, env_flat(env0_h), n_iter=n_iter, max_steps=3)
+
+    def fun(x):
+        E, g = evaluate([x.reshape(A0.shape)[0]], w.Lx, w.Ly, w.chi, n_iter, w.terms, env0=env0_h, grad=True)
+        return E, np.asarray(g[0]).ravel()
+
+    ref = lbfgs(fun, A0.ravel(), max_iter=3)
+    assert gpu.n_iter == ref.n_iter == 3
+    assert np.allclose(gpu.history, ref.history, rtol=0, atol=1e-8), (gpu.history, ref.history)
+    assert gpu.history[-1] < gpu.history[0]

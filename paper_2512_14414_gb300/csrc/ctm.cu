@@ -38,6 +38,7 @@
 // forward), and back-propagates through it (Eq. AD).
 #include <array>
 #include <cmath>
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -484,60 +485,62 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
     int l = std::min(r, std::max(chi + 16, 32));
     bool sketched = false;
     if (h->debug_sweeps) CTM_CUDA(cudaMemsetAsync(h->dsweeps, 0, sizeof(int), st));
-    std::vector<char> done(nb, 0);
-    sketched = true;
-    for (int b0 = 0; b0 < nb && sketched; ++b0) {
-      if (done[b0]) continue;
-      std::vector<int> grp;
-      for (int b = b0; b < nb; ++b)
-        if (!done[b] && in[b].n_r == in[b0].n_r && in[b].n_l == in[b0].n_l) grp.push_back(b), done[b] = 1;
-      const int nr = (int)in[b0].n_r, nl = (int)in[b0].n_l, ng = (int)grp.size();
-      int hmax = 0;
+    // all pairs of the column step in one batch (different n_r are padded inside the sketch)
+    {
+      int hmax = 0, nrmax = 0;
       bool known = true;
-      for (int b : grp) hmax = std::max(hmax, hint[h->cur_pair + b]), known = known && hint[h->cur_pair + b] > 0;
+      std::vector<int> nrs(nb), nls(nb);
+      for (int b = 0; b < nb; ++b) {
+        hmax = std::max(hmax, hint[h->cur_pair + b]);
+        known = known && hint[h->cur_pair + b] > 0;
+        nrs[b] = (int)in[b].n_r;
+        nls[b] = (int)in[b].n_l;
+        nrmax = std::max(nrmax, nrs[b]);
+      }
+      int nlmax = *std::max_element(nls.begin(), nls.end());
       l = known ? std::min(r, std::max(16, (hmax + 12 + 7) / 8 * 8)) : std::min(r, std::max(chi + 16, 32));
-      std::vector<const double*> Np(ng), Sp(ng);
-      for (int g = 0; g < ng; ++g) Np[g] = (const double*)N64[grp[g]].p, Sp[g] = (const double*)S64[grp[g]].p;
+      std::vector<const double*> Np(nb), Sp(nb);
+      for (int b = 0; b < nb; ++b) Np[b] = (const double*)N64[b].p, Sp[b] = (const double*)S64[b].p;
       // warm start from the same pair's right singular vectors of the previous iteration
-      std::vector<const double*> Wp(ng, nullptr);
+      std::vector<const double*> Wp(nb, nullptr);
       int kw = 0, ldw = 0;
       if (known && h->cur_iter > 0 && (int)h->fac[h->cur_iter - 1].size() >= h->cur_pair + nb) {
         auto& prev = h->fac[h->cur_iter - 1];
         bool same = true;
-        for (int g = 0; g < ng; ++g) {
-          const ctm_handle::Fac& f = prev[h->cur_pair + grp[g]];
-          same = same && f.V && f.n_r == nr && f.rs == prev[h->cur_pair + grp[0]].rs;
+        for (int b = 0; b < nb; ++b) {
+          const ctm_handle::Fac& f = prev[h->cur_pair + b];
+          same = same && f.V && f.n_r == nrs[b] && f.rs == prev[h->cur_pair].rs;
         }
         if (same) {
-          ldw = prev[h->cur_pair + grp[0]].rs;
+          ldw = prev[h->cur_pair].rs;
           kw = std::min(hmax, ldw);
-          for (int g = 0; g < ng; ++g) Wp[g] = prev[h->cur_pair + grp[g]].V;
+          for (int b = 0; b < nb; ++b) Wp[b] = prev[h->cur_pair + b].V;
         }
       }
       bool ok = false;
       for (int attempt = 0; attempt < 2 && !ok && 2 * l <= r; ++attempt) {
-        double* ws = (double*)E.arena().alloc(svd_sketch_product_ws(ng, nr, nl, l));
-        double* lam = (double*)E.arena().alloc(sizeof(double) * ng * l);
-        double* Uo = (double*)E.arena().alloc(sizeof(double) * ng * (int64_t)nr * l);
-        double* Vo = (double*)E.arena().alloc(sizeof(double) * ng * (int64_t)nr * l);
+        double* ws = (double*)E.arena().alloc(svd_sketch_product_ws(nb, nrmax, nlmax, l));
+        double* lam = (double*)E.arena().alloc(sizeof(double) * nb * l);
+        double* Uo = (double*)E.arena().alloc(sizeof(double) * nb * (int64_t)nrmax * l);
+        double* Vo = (double*)E.arena().alloc(sizeof(double) * nb * (int64_t)nrmax * l);
         std::vector<int> inc, rk;
         const int kwa = std::min(kw, l - 8);
-        svd_sketch_product(Np.data(), Sp.data(), ng, nr, nl, l, kwa > 0 ? Wp.data() : nullptr, ldw, std::max(kwa, 0), ws,
-                           lam, Uo, Vo, h->dstatus, h->dsweeps, inc, rk, st);
+        svd_sketch_product(Np.data(), Sp.data(), nrs.data(), nls.data(), nb, l, kwa > 0 ? Wp.data() : nullptr, ldw,
+                           std::max(kwa, 0), ws, lam, Uo, Vo, h->dstatus, h->dsweeps, inc, rk, st);
         ok = true;
         for (int x : inc) ok = ok && x == 0;
         if (!ok) {
           l *= 2;
           continue;
         }
-        for (int g = 0; g < ng; ++g) {
-          ctm_handle::Fac* f = F[grp[g]];
+        for (int b = 0; b < nb; ++b) {
+          ctm_handle::Fac* f = F[b];
           f->rs = l;
-          hint[h->cur_pair + grp[g]] = rk[g];
-          const size_t nb_uv = sizeof(double) * (size_t)nr * l;
-          CTM_CUDA(cudaMemcpyAsync(f->lam, lam + (int64_t)g * l, sizeof(double) * l, cudaMemcpyDeviceToDevice, st));
-          CTM_CUDA(cudaMemcpyAsync(f->U, Uo + (int64_t)g * nr * l, nb_uv, cudaMemcpyDeviceToDevice, st));
-          CTM_CUDA(cudaMemcpyAsync(f->V, Vo + (int64_t)g * nr * l, nb_uv, cudaMemcpyDeviceToDevice, st));
+          hint[h->cur_pair + b] = rk[b];
+          const size_t nb_uv = sizeof(double) * (size_t)nrs[b] * l;  // the first n_r rows of the padded block
+          CTM_CUDA(cudaMemcpyAsync(f->lam, lam + (int64_t)b * l, sizeof(double) * l, cudaMemcpyDeviceToDevice, st));
+          CTM_CUDA(cudaMemcpyAsync(f->U, Uo + (int64_t)b * nrmax * l, nb_uv, cudaMemcpyDeviceToDevice, st));
+          CTM_CUDA(cudaMemcpyAsync(f->V, Vo + (int64_t)b * nrmax * l, nb_uv, cudaMemcpyDeviceToDevice, st));
         }
       }
       sketched = ok;

@@ -369,21 +369,22 @@ void gemm_t(const T* A, const T* B, T* C, const GemmSpec& g, cudaStream_t st) {
       for (int64_t m = 0; m < g.M; ++m) CTM_CUDA(cudaMemsetAsync(C + b * g.strideC + m * g.ldc, 0, g.N * sizeof(T), st));
     return;
   }
-  // Tile: 64 x 64, or 32 x 32 for FP64 products with a short side (the FP64 pipe is the
-  // bound there, so padded rows cost real time) and for FP32 products whose 64 x 64 tiles would
-  // not cover the SMs.  K is split when the output tiles alone
-  // cannot fill the GPU: FP64 down to 16-wide chunks, FP32 down to 128-wide chunks (up to
-  // 256 of them for outputs of a few elements with a long K).
-  const bool small = sizeof(T) == 8 ? (g.M < 128 || g.N < 128)
-                                     : (g.M < 64 || g.N < 64 ||
-                                        g.batch * ((g.M + 63) / 64) * ((g.N + 63) / 64) < num_sms());
-  const int64_t BT = small ? 32 : 64;
-  const int64_t tiles = g.batch * ((g.M + BT - 1) / BT) * ((g.N + BT - 1) / BT);
-  const int64_t min_chunk = sizeof(T) == 8 ? 16 : 128;
+  // Tile: the largest of 64, 32 and 16 whose output tiles cover the SMs (FP64 is issue-bound at
+  // about 2 FMA/clk/SM, so a product must reach every SM; FP32 stops at 32, where latency rather
+  // than arithmetic is the limit).  K is then split while the tiles alone cannot fill the GPU:
+  // FP64 into chunks of at least 16 (when K >= 64), FP32 into chunks of at least 64 (up to 256
+  // chunks for outputs of a few elements with a long K).
+  auto ntiles = [&](int64_t bt) { return g.batch * ((g.M + bt - 1) / bt) * ((g.N + bt - 1) / bt); };
+  const int64_t sms = num_sms();
+  int64_t BT = 64;
+  if (ntiles(64) < (sizeof(T) == 8 ? 2 : 1) * sms || g.M < 64 || g.N < 64) BT = 32;
+  if (sizeof(T) == 8 && BT == 32 && (ntiles(32) < sms || g.M < 32 || g.N < 32)) BT = 16;
+  const int64_t tiles = ntiles(BT);
+  const int64_t min_chunk = sizeof(T) == 8 ? 16 : 64;
   const int64_t max_split = sizeof(T) == 8 ? 64 : (tiles <= 4 ? 256 : 32);
   int64_t nsplit = 1;
-  if (tiles < 2 * num_sms() && g.K >= 2 * min_chunk) {
-    nsplit = std::min<int64_t>({(2 * num_sms() + tiles - 1) / tiles, g.K / min_chunk, max_split});
+  if (tiles < 2 * sms && g.K >= (sizeof(T) == 8 ? 64 : 2 * min_chunk)) {
+    nsplit = std::min<int64_t>({(2 * sms + tiles - 1) / tiles, g.K / min_chunk, max_split});
     // workspace bound: 256 MB of partial tiles
     nsplit = std::min<int64_t>(nsplit, std::max<int64_t>(1, (int64_t(256) << 20) / ((int64_t)sizeof(T) * g.batch * g.M * g.N)));
     if (nsplit < 2) nsplit = 1;
@@ -396,7 +397,9 @@ void gemm_t(const T* A, const T* B, T* C, const GemmSpec& g, cudaStream_t st) {
   CTM_CHECK((g.N + BT - 1) / BT < (int64_t(1) << 31), CTM_ERR_INVALID_ARG, "gemm N too large");
   dim3 grid((unsigned)((g.N + BT - 1) / BT), (unsigned)std::min<int64_t>(work, 65535),
             (unsigned)std::min<int64_t>((work + 65534) / 65535, 65535));
-  if (small)
+  if (BT == 16)
+    gemm_simt<T, 1, 1, 16><<<grid, 256, 0, st>>>(A, B, out, g, nsplit, kchunk);
+  else if (BT == 32)
     gemm_simt<T, 2, 2, 16><<<grid, 256, 0, st>>>(A, B, out, g, nsplit, kchunk);
   else
     gemm_simt<T, 4, 4, 16><<<grid, 256, 0, st>>>(A, B, out, g, nsplit, kchunk);

@@ -97,10 +97,12 @@ size_t svd_sketch_product_ws(int batch, int nr, int nl, int l);
 // warm (nullable): per matrix an n_r x kw block (row-major, ld ldw) that replaces the first kw
 // columns of the random test matrix -- the previous right singular vectors, so that rho Omega
 // is already close to U Sigma and the Jacobi sweeps start near convergence.
-void svd_sketch_product(const double* const* N, const double* const* S, int batch, int nr, int nl, int l,
-                        const double* const* warm, int ldw, int kw, double* ws, double* lam, double* Uo, double* Vo,
-                        int* status, int* sweeps_out, std::vector<int>& incomplete_host, std::vector<int>& rank_host,
-                        cudaStream_t st);
+// nrs / nls: per matrix n_r and n_l (host arrays); ws from svd_sketch_product_ws(batch, max n_r,
+// max n_l, l); Uo / Vo hold batch x (max n_r) x l, rows beyond a matrix's own n_r zero.
+void svd_sketch_product(const double* const* N, const double* const* S, const int* nrs, const int* nls, int batch,
+                        int l, const double* const* warm, int ldw, int kw, double* ws, double* lam, double* Uo,
+                        double* Vo, int* status, int* sweeps_out, std::vector<int>& incomplete_host,
+                        std::vector<int>& rank_host, cudaStream_t st);
 // Flops counted by the Jacobi kernels since the last call (6r per pair test, 12r per rotation).
 double jacobi_flops_read_reset(cudaStream_t st);
 // X[k*m + i] = U[i*r + k] for i < r, 0 for r <= i < m  (k < r): [U; 0] stored column-major.

@@ -665,10 +665,15 @@ size_t svd_sketch_product_ws(int batch, int nr, int nl, int l) {
   return sizeof(double) * batch * per + sizeof(int) * 2 * batch + 256;
 }
 
-void svd_sketch_product(const double* const* N, const double* const* S, int batch, int nr, int nl, int l,
-                        const double* const* warm, int ldw, int kw, double* ws, double* lam, double* Uo, double* Vo,
-                        int* status, int* sweeps_out, std::vector<int>& incomplete_host, std::vector<int>& rank_host,
-                        cudaStream_t st) {
+void svd_sketch_product(const double* const* N, const double* const* S, const int* nrs, const int* nls, int batch,
+                        int l, const double* const* warm, int ldw, int kw, double* ws, double* lam, double* Uo,
+                        double* Vo, int* status, int* sweeps_out, std::vector<int>& incomplete_host,
+                        std::vector<int>& rank_host, cudaStream_t st) {
+  // Matrices of different n_r share one batch: every n_r-long object is stored with the batch's
+  // largest n_r and zero rows below its own; zero rows change neither the Householder QR nor
+  // the one-sided Jacobi rotations, and they come out as zero rows of U and V.
+  int nr = 0, nl = 0;
+  for (int b = 0; b < batch; ++b) nr = std::max(nr, nrs[b]), nl = std::max(nl, nls[b]);
   const int64_t Ln = (int64_t)nl * l, Lr = (int64_t)nr * l, ll = (int64_t)l * l;
   const double* omega = sketch_omega(Lr, st);
   double* T = ws;                    // S^t Omega, n_l x l row-major
@@ -680,21 +685,28 @@ void svd_sketch_product(const double* const* N, const double* const* S, int batc
   double* Ul = Vl + batch * ll;      // l x l sorted
   double* tau = Ul + batch * ll;     // l per matrix
   int* inc = (int*)(tau + batch * l);
+  bool ragged = false;
+  for (int b = 0; b < batch; ++b) ragged = ragged || nrs[b] != nr;
+  if (ragged) {
+    CTM_CUDA(cudaMemsetAsync(Yt, 0, sizeof(double) * batch * Lr, st));
+    CTM_CUDA(cudaMemsetAsync(Bt, 0, sizeof(double) * batch * Lr, st));
+  }
   GemmSpec g;
   if (!warm) kw = 0;
   for (int b = 0; b < batch; ++b) {
+    const int mr = nrs[b], ml = nls[b];
     // T = S^t Omega, Omega = [warm_b(:, :kw) | random columns]
     if (kw > 0) {
       g = GemmSpec();
-      g.M = nl; g.N = kw; g.K = nr; g.transA = true; g.lda = nl; g.ldb = ldw; g.ldc = l;
+      g.M = ml; g.N = kw; g.K = mr; g.transA = true; g.lda = ml; g.ldb = ldw; g.ldc = l;
       gemm_f64(S[b], warm[b], T + b * Ln, g, st);
     }
     g = GemmSpec();
-    g.M = nl; g.N = l - kw; g.K = nr; g.transA = true; g.lda = nl; g.ldb = l; g.ldc = l;
+    g.M = ml; g.N = l - kw; g.K = mr; g.transA = true; g.lda = ml; g.ldb = l; g.ldc = l;
     gemm_f64(S[b], omega + kw, T + b * Ln + kw, g, st);
     // Y^t = T^t N^t
     g = GemmSpec();
-    g.M = l; g.N = nr; g.K = nl; g.transA = true; g.lda = l; g.transB = true; g.ldb = nl; g.ldc = nr;
+    g.M = l; g.N = mr; g.K = ml; g.transA = true; g.lda = l; g.transB = true; g.ldb = ml; g.ldc = nr;
     gemm_f64(T + b * Ln, N[b], Yt + b * Lr, g, st);
   }
   qr_householder(Yt, tau, batch, nr, l, Lr, status, st);
@@ -702,13 +714,14 @@ void svd_sketch_product(const double* const* N, const double* const* S, int batc
   CTM_LAUNCHED();
   qr_apply_Q(Yt, tau, Qc, batch, nr, l, l, Lr, Lr, status, st);
   for (int b = 0; b < batch; ++b) {
-    // Z = Q^t N (Qc read row-major is Q^t)
+    const int mr = nrs[b], ml = nls[b];
+    // Z = Q^t N (Qc read row-major is Q^t; its rows beyond mr are zero)
     g = GemmSpec();
-    g.M = l; g.N = nl; g.K = nr; g.lda = nr; g.ldb = nl; g.ldc = nl;
+    g.M = l; g.N = ml; g.K = mr; g.lda = nr; g.ldb = ml; g.ldc = nl;
     gemm_f64(Qc + b * Lr, N[b], Z + b * Ln, g, st);
     // B = Z S^t
     g = GemmSpec();
-    g.M = l; g.N = nr; g.K = nl; g.lda = nl; g.transB = true; g.ldb = nl; g.ldc = nr;
+    g.M = l; g.N = mr; g.K = ml; g.lda = nl; g.transB = true; g.ldb = ml; g.ldc = nr;
     gemm_f64(Z + b * Ln, S[b], Bt + b * Lr, g, st);
   }
   ensure_coop(batch, st);

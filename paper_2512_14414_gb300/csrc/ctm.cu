@@ -51,7 +51,6 @@
 namespace ctm {
 namespace {
 
-constexpr double kRankTol = 1e-13;
 constexpr int kMaxSweeps = 60;
 
 enum Kind { KET = 0, YS = 1, XS = 2, BRA = 3 };
@@ -112,6 +111,7 @@ struct ctm_handle {
   int R = 0, C = 0, nsites = 0;
   ctm::DType edt = ctm::F64;
   double cut = 1e-5, eps = 1e-30;
+  double rank_tol = 1e-13;  // triplets below rank_tol * s_1 are left out of the adjoint's core
   int64_t launches = 0;
   cudaStream_t st = nullptr;
   std::unique_ptr<ctm::Arena> persist, tape, store;
@@ -553,6 +553,7 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
       CTM_CUDA(cudaMemcpyAsync(&sw, h->dsweeps, sizeof(int), cudaMemcpyDeviceToHost, st));
       CTM_CUDA(cudaStreamSynchronize(st));
       int rk_floor = 0, rk_cut = 0;  // largest numerical rank (1e-14) and kept count (cutoff) of the batch
+      std::string kept_list;
       for (int b = 0; b < nb; ++b) {
         std::vector<double> lh(F[b]->rs);
         CTM_CUDA(cudaMemcpy(lh.data(), F[b]->lam, sizeof(double) * lh.size(), cudaMemcpyDeviceToHost));
@@ -560,9 +561,15 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
         for (double v : lh) a += v > 1e-14 * lh[0], c += v > h->cut * lh[0];
         rk_floor = std::max(rk_floor, a);
         rk_cut = std::max(rk_cut, c);
+        kept_list += " " + std::to_string(c);
+        // distance of the nearest singular value to the cutoff, in units of the cutoff
+        double near = 1e300;
+        for (double v : lh) near = std::min(near, std::fabs(v / lh[0] / h->cut - 1.0));
+        kept_list += "(" + std::to_string(near).substr(0, 6) + ")";
       }
-      fprintf(stderr, "libctm: iteration %d pairs %d..%d r=%d %s l=%d Jacobi sweeps %d rank %d above cutoff %d\n",
-              h->cur_iter, h->cur_pair, h->cur_pair + nb - 1, r, sketched ? "sketch" : "full", l, sw, rk_floor, rk_cut);
+      fprintf(stderr, "libctm: iteration %d pairs %d..%d r=%d %s l=%d Jacobi sweeps %d rank %d above cutoff %d kept%s\n",
+              h->cur_iter, h->cur_pair, h->cur_pair + nb - 1, r, sketched ? "sketch" : "full", l, sw, rk_floor, rk_cut,
+              kept_list.c_str());
     }
     // canonical signs keep the environment's chi basis fixed from one iteration to the next
     for (int b = 0; b < nb; ++b) sign_fix(F[b]->U, F[b]->V, 1, in[b].n_r, F[b]->rs, st);
@@ -581,7 +588,7 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
     s.sinv = (double*)E.arena().alloc(sizeof(double) * rs);
     s.Wp = (double*)E.arena().alloc(sizeof(double) * nr * kb);
     s.Zp = (double*)E.arena().alloc(sizeof(double) * nr * kb);
-    proj_prepare(F[b]->lam, F[b]->U, F[b]->V, s.inv, s.sinv, 1, nr, rs, kb, h->cut, kRankTol, h->dstatus, st);
+    proj_prepare(F[b]->lam, F[b]->U, F[b]->V, s.inv, s.sinv, 1, nr, rs, kb, h->cut, h->rank_tol, h->dstatus, st);
     scale_cols(F[b]->V, rs, 0, s.inv, 0, s.Wp, 1, nr, kb, st);
     scale_cols(F[b]->U, rs, 0, s.inv, 0, s.Zp, 1, nr, kb, st);
     Tensor P64 = E.zeros(F64, {nl, (int64_t)chi});
@@ -611,10 +618,10 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
   for (int b = 0; b < nb; ++b) Fc[b] = *F[b];
   std::vector<PairIn> inc = in;
   std::vector<Tensor> Pc = P, Qc = Q;
-  const double eps = h->eps;
+  const double eps = h->eps, rank_tol = h->rank_tol;
   const DType edt = h->edt;
   ctm_handle* hh = h;
-  E.push([hh, &E, inc, N64, S64, Fc, sv, Pc, Qc, kept, chi, eps, edt, st]() {
+  E.push([hh, &E, inc, N64, S64, Fc, sv, Pc, Qc, kept, chi, eps, rank_tol, edt, st]() {
     for (size_t b = 0; b < inc.size(); ++b) {
       void* gP = E.grad(Pc[b], false);
       void* gQ = E.grad(Qc[b], false);
@@ -659,7 +666,7 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
       gemm_f64(U, dUk, Aa, g, st);
       gemm_f64(V, dVk, Bb, g, st);
       double* core = A64((int64_t)rs * rs);
-      proj_core(Aa, Bb, lam, dl, core, 1, rs, kb, kRankTol, eps, st);
+      proj_core(Aa, Bb, lam, dl, core, 1, rs, kb, rank_tol, eps, st);
       double* Xu = A64(nr * kb);
       double* Xv = A64(nr * kb);
       g = GemmSpec();

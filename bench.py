@@ -268,6 +268,7 @@ def main():
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
     launches = ctm.kernel_launches - launches0
+    free_b, total_b = torch.cuda.mem_get_info(dev)  # device memory held once the steps are done
     # One more step of the same workload with a CUDA-event pair around every launch (on the stream
     # each kernel is launched on): per-class device time, launch counts and algorithmic work for
     # the roofline.  Kept out of the K timed steps because the events themselves cost ~15%.
@@ -359,6 +360,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),
+        "device_mem_used_gb": round((total_b - free_b) / 1e9, 2),
         "clocks": ck,
     }
     print(json.dumps(line), flush=True)

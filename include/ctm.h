@@ -71,7 +71,7 @@ typedef enum {
   CTM_TF32 = 1,    /* contractions TF32 x TF32 -> FP32 on the tensor cores */
   CTM_BF16 = 2,    /* contractions BF16 x BF16 -> FP32 on the tensor cores */
   CTM_TF32X3 = 3,  /* error-compensated TF32 (hi*hi + hi*lo + lo*hi) */
-  CTM_BF16X3 = 4   /* error-compensated BF16 */
+  CTM_BF16X3 = 4   /* error-compensated BF16 (hi*hi + hi*lo + lo*hi, ~16 significant bits) */
 } ctm_precision;
 
 /* Bond kinds, relative to PEPS site (x, y):

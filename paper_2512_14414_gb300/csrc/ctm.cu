@@ -1161,7 +1161,11 @@ int ctm_init(ctm_handle* h, const double* A, const double* env0, void* stream) {
     h->st = (cudaStream_t)stream;
     ctm::ensure_device(h);
     h->eng->set_stream(h->st);
-    const int tcm = h->d.precision == CTM_TF32 ? 1 : h->d.precision == CTM_BF16 ? 2 : h->d.precision == CTM_TF32X3 ? 3 : 0;
+    const int tcm = h->d.precision == CTM_TF32     ? 1
+                    : h->d.precision == CTM_BF16   ? 2
+                    : h->d.precision == CTM_TF32X3 ? 3
+                    : h->d.precision == CTM_BF16X3 ? 4
+                                                   : 0;
     // CTM_TC_MIN_MNK (read at every ctm_init) moves the size threshold of the tensor-core route
     const char* tmin = getenv("CTM_TC_MIN_MNK");
     h->eng->set_tc(tcm, h->dstatus, tmin && *tmin ? (int64_t)atoll(tmin) : (int64_t(1) << 26));

@@ -224,7 +224,7 @@ void Engine::einsum_into(const Tensor& A, const Labels& la, const Tensor& B, con
   const bool tc = A.dt == F32 && tc_mode_ != 0 && KK0 >= 8 && nb0 <= 65535 &&
                   nb0 * MM0 * NN0 * KK0 >= tc_min_mnk_ && MM0 >= 32 && NN0 >= 32 &&
                   (tiles0 >= 8 || tc_min_mnk_ == 0) &&
-                  (KK0 * (tc_mode_ == 2 ? 2 : 4)) % 16 == 0;  // modes: 1 tf32, 2 bf16, 3 tf32x3
+                  (KK0 * (tc_mode_ == 2 || tc_mode_ == 4 ? 2 : 4)) % 16 == 0;  // 1 tf32, 2 bf16, 3 tf32x3, 4 bf16x3
   if (tc) {
     einsum_tc(A, la, B, lb, lc, out, accumulate, dims, batch, M, N, K, Mlc, Nlc, Klb, nC);
     return;
@@ -363,7 +363,18 @@ void Engine::einsum_tc(const Tensor& A, const Labels& la, const Tensor& B, const
   void* Cp = best.permC ? arena_->alloc(nC * 4) : out;
   const double beta = (!best.permC && accumulate) ? 1.0 : 0.0;
   gemm_flops_ += 2 * nb * MM * NN * KK;
-  if (tc_mode_ == 3) {
+  if (tc_mode_ == 4) {
+    void* Ah = arena_->alloc(nA * 2);
+    void* Al = arena_->alloc(nA * 2);
+    void* Bh = arena_->alloc(nB * 2);
+    void* Bl = arena_->alloc(nB * 2);
+    split_bf16((const float*)Ap, Ah, Al, nA, st_);
+    split_bf16((const float*)Bp, Bh, Bl, nB, st_);
+    if (!best.swap)
+      gemm_tc_x3_bf16(Ah, Al, Bh, Bl, (float*)Cp, MM, NN, KK, nb, beta, tc_status_, st_);
+    else
+      gemm_tc_x3_bf16(Bh, Bl, Ah, Al, (float*)Cp, NN, MM, KK, nb, beta, tc_status_, st_);
+  } else if (tc_mode_ == 3) {
     float* Ah = (float*)arena_->alloc(nA * 4);
     float* Al = (float*)arena_->alloc(nA * 4);
     float* Bh = (float*)arena_->alloc(nB * 4);

@@ -93,7 +93,8 @@ class Engine {
   Tensor permute(const Tensor& x, const std::vector<int>& perm);  // out dim k = in dim perm[k]
 
   // Tensor-core mode of FP32 contractions: 0 SIMT FP32, 1 TF32 (tcgen05 kind::tf32),
-  // 2 BF16 operands (tcgen05 kind::f16).  `status` receives device-side error bits.
+  // 2 BF16 operands (tcgen05 kind::f16), 3 error-compensated TF32 (three products),
+  // 4 error-compensated BF16.  `status` receives device-side error bits.
   // Products of fewer than min_mnk multiply-adds (batch * M * N * K) stay on the CUDA cores.
   void set_tc(int mode, int* status, int64_t min_mnk) {
     tc_mode_ = mode;

@@ -664,6 +664,17 @@ __global__ void split_tf32_k(const float* x, float* hi, float* lo, int64_t n) {
   }
 }
 
+// x = hi + lo with hi = x rounded to BF16 and lo = (x - hi) rounded to BF16 (about 16
+// significant bits in all; the rest of x is dropped).
+__global__ void split_bf16_k(const float* x, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = x[i];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[i] = h;
+    lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
 __global__ void embed_t_k(const double* U, int r, double* X, int64_t m) {
   int64_t total = (int64_t)r * m;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -820,6 +831,13 @@ void split_tf32(const float* x, float* hi, float* lo, int64_t n, cudaStream_t st
   if (n == 0) return;
   ProfScope prof(PROF_PERMUTE, st, 0.0, 12.0 * n, prof_tag("split_tf32", 1, n, 0, 0));
   split_tf32_k<<<nblocks(n, 256), 256, 0, st>>>(x, hi, lo, n);
+  CTM_LAUNCHED();
+}
+
+void split_bf16(const float* x, void* hi, void* lo, int64_t n, cudaStream_t st) {
+  if (n == 0) return;
+  ProfScope prof(PROF_PERMUTE, st, 0.0, 8.0 * n, prof_tag("split_bf16", 1, n, 0, 0));
+  split_bf16_k<<<nblocks(n, 256), 256, 0, st>>>(x, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo, n);
   CTM_LAUNCHED();
 }
 

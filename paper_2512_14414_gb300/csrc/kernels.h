@@ -38,6 +38,11 @@ void gemm_tc_x3(const float* Ahi, const float* Alo, const float* Bhi, const floa
                 int64_t N, int64_t K, int64_t batch, double beta, int* status, cudaStream_t st);
 // hi = x rounded to TF32, lo = (x - hi) rounded to TF32.
 void split_tf32(const float* x, float* hi, float* lo, int64_t n, cudaStream_t st);
+// Error-compensated BF16: C (+)= Ahi Bhi^t + Ahi Blo^t + Alo Bhi^t, operands BF16 (split_bf16).
+void gemm_tc_x3_bf16(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, float* C, int64_t M,
+                     int64_t N, int64_t K, int64_t batch, double beta, int* status, cudaStream_t st);
+// hi = x rounded to BF16, lo = (x - hi) rounded to BF16 (BF16 outputs).
+void split_bf16(const float* x, void* hi, void* lo, int64_t n, cudaStream_t st);
 
 // ------------------------------------------------------------------ elementwise / reductions
 void fill(void* p, DType t, int64_t n, double v, cudaStream_t st);

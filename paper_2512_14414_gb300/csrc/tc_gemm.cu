@@ -336,4 +336,17 @@ void gemm_tc_x3(const float* Ahi, const float* Alo, const float* Bhi, const floa
   launch_tc<false, true>(ma, mb, ma2, mb2, C, M, N, batch, K, (float)beta, status, st);
 }
 
+void gemm_tc_x3_bf16(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, float* C, int64_t M,
+                     int64_t N, int64_t K, int64_t batch, double beta, int* status, cudaStream_t st) {
+  if (M == 0 || N == 0 || batch == 0) return;
+  CTM_CHECK(tc_gemm_ok(true, M, N, K, Ahi, Bhi) && tc_gemm_ok(true, M, N, K, Alo, Blo), CTM_ERR_INVALID_ARG,
+            "tc gemm bf16 x3: unsupported shape/alignment");
+  CTM_CHECK(batch <= 65535, CTM_ERR_INVALID_ARG, "tc gemm: batch too large");
+  ProfScope ps(PROF_TC, st, 2.0 * batch * M * N * K, (double)batch * (4.0 * (M * K + N * K) + 4.0 * M * N),
+               prof_tag("tc_bf16x3", batch, M, N, K, beta != 0.0));
+  CUtensorMap ma = make_map(Ahi, true, M, K, batch), mb = make_map(Bhi, true, N, K, batch);
+  CUtensorMap ma2 = make_map(Alo, true, M, K, batch), mb2 = make_map(Blo, true, N, K, batch);
+  launch_tc<true, true>(ma, mb, ma2, mb2, C, M, N, batch, K, (float)beta, status, st);
+}
+
 }  // namespace ctm

@@ -124,3 +124,20 @@ def test_plain_tf32_and_bf16_run_and_stay_close_in_energy(monkeypatch):
     for prec, tol in (("tf32", 1e-3), ("bf16", 1e-2)):
         E, _, _ = gpu_energy_grad(w, w.n_iter, precision=prec)
         assert abs(E - Er) <= tol, (prec, E, Er)
+
+
+def test_bf16x3_tensor_core_mode_runs_and_tracks_the_oracle(monkeypatch):
+    # error-compensated BF16 (hi*hi + hi*lo + lo*hi, about 16 significant bits) with every
+    # eligible product forced onto the tcgen05 kernel: coarser than TF32x3, held to 1e-4
+    monkeypatch.setenv("CTM_TC_MIN_MNK", "0")
+    w = W.config("heis_d4_chi32")
+    n_iter = 10
+    ctm = make_ctm(w, "bf16x3")
+    ctm.init(site_stack(w.tensors), env_flat(W.initial_environment(w)))
+    ctm.profile(True)
+    e, _ = ctm.grad(n_iter)
+    prof = ctm.profile_read()
+    ctm.profile(False)
+    assert prof["tc_gemm"][1] > 0
+    Er, _ = oracle_energy_grad(w, n_iter, grad=False)
+    assert abs(float(e[0]) - Er) <= 1e-4, (float(e[0]), Er)

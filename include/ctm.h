@@ -177,6 +177,21 @@ int ctm_svd(const double* M, int batch, int r, double* U, double* s, double* V, 
  * Synchronises the stream to read the status. */
 int ctm_svd_noalloc(const double* M, int batch, int r, double* U, double* s, double* V, void* stream);
 
+/* Forward pass of the warm-start network: an MLP that maps the flattened site tensors to an
+ * initial environment, so that the CTMRG iterations of Sec. SLF (step ii) start near their
+ * fixed point.  The paper has no counterpart (it starts from a fixed environment); the network
+ * and its training live in paper_2512_14414_gb300/warmstart.py.
+ *   x    : device, FP32, batch x dims[0] (row-major).
+ *   W[k] : device, FP32, dims[k+1] x dims[k] row-major (torch.nn.Linear layout), k < n_layers;
+ *          W itself is a HOST array of device pointers.
+ *   b[k] : device, FP32, dims[k+1] entries, or b == NULL (no biases).
+ *   work : device, FP32, at least 2 * batch * max(dims[1..n_layers-1]) floats (caller-owned).
+ *   y    : device, FP32, batch x dims[n_layers].
+ * Hidden layers apply GELU (exact, erf form) after the bias; the last layer is linear.
+ * 1 <= n_layers <= 16.  Enqueued on the stream; no allocation. */
+int ctm_mlp_forward(const float* x, int batch, int n_layers, const int* dims, const float* const* W,
+                    const float* const* b, float* work, float* y, void* stream);
+
 int ctm_destroy(ctm_handle* h);
 const char* ctm_error_string(int status);
 

@@ -1367,6 +1367,16 @@ int ctm_profile_read(ctm_handle* h, int cls, double* ms, int64_t* launches, doub
   });
 }
 
+int ctm_mlp_forward(const float* x, int batch, int n_layers, const int* dims, const float* const* W,
+                    const float* const* b, float* work, float* y, void* stream) {
+  if (!x || !y || !dims || !W || !work || batch < 1 || n_layers < 1 || n_layers > 16) return CTM_ERR_INVALID_ARG;
+  for (int k = 0; k <= n_layers; ++k)
+    if (dims[k] < 1) return CTM_ERR_INVALID_ARG;
+  for (int k = 0; k < n_layers; ++k)
+    if (!W[k]) return CTM_ERR_INVALID_ARG;
+  return guard(nullptr, [&]() { ctm::mlp_forward(x, batch, n_layers, dims, W, b, work, y, (cudaStream_t)stream); });
+}
+
 int ctm_svd(const double* M, int batch, int r, double* U, double* s, double* V, void* stream) {
   if (!M || !U || !s || !V || batch < 1 || r < 1 || r > 4096) return CTM_ERR_INVALID_ARG;
   return guard(nullptr, [&]() {

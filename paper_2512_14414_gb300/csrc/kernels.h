@@ -41,6 +41,10 @@ void split_tf32(const float* x, float* hi, float* lo, int64_t n, cudaStream_t st
 // Error-compensated BF16: C (+)= Ahi Bhi^t + Ahi Blo^t + Alo Bhi^t, operands BF16 (split_bf16).
 void gemm_tc_x3_bf16(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, float* C, int64_t M,
                      int64_t N, int64_t K, int64_t batch, double beta, int* status, cudaStream_t st);
+// MLP forward (FP32): hidden layers Linear + GELU, last layer Linear; W[k] is [dims[k+1]][dims[k]],
+// b[k] has dims[k+1] entries (b may be null); work holds 2 * batch * max hidden width floats.
+void mlp_forward(const float* x, int batch, int n_layers, const int* dims, const float* const* W,
+                 const float* const* b, float* work, float* y, cudaStream_t st);
 // hi = x rounded to BF16, lo = (x - hi) rounded to BF16 (BF16 outputs).
 void split_bf16(const float* x, void* hi, void* lo, int64_t n, cudaStream_t st);
 

@@ -172,3 +172,44 @@ def optimize_peps(ctm, A0: np.ndarray, env0, n_iter: int, max_steps: int = 20, m
         return float(e[0]), dA.detach().cpu().numpy().ravel()
 
     return lbfgs(fun, A0.ravel(), m=m, max_iter=max_steps, callback=callback)
+
+
+def main():
+    """Optimise a workload's PEPS with the GPU energy and gradient; one JSON line per step."""
+    import argparse
+    import json
+    import time
+
+    import torch
+
+    import workloads as W
+    from .api import CTM
+
+    ap = argparse.ArgumentParser(description="L-BFGS on the nested single-layer CTMRG energy")
+    ap.add_argument("--workload", default="ss_d6_chi64")
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--history", type=int, default=10)
+    ap.add_argument("--precision", default="tf32x3")
+    ap.add_argument("--n-iter", type=int, default=None)
+    args = ap.parse_args()
+    w = W.config(args.workload)
+    n_iter = args.n_iter or w.n_iter
+    ctm = CTM(w.Lx, w.Ly, w.d, w.D, w.chi, [(t.x, t.y, t.kind, t.coupling, t.h) for t in w.terms],
+              precision=args.precision)
+    env0 = torch.tensor(np.concatenate([a.ravel() for s in W.initial_environment(w) for a in s]),
+                        dtype=torch.float64, device="cuda")
+    t0 = time.perf_counter()
+
+    def report(res):
+        print(json.dumps({"step": res.n_iter, "energy": res.f, "grad_norm": float(np.linalg.norm(res.g)),
+                          "evaluations": res.n_eval, "elapsed_s": time.perf_counter() - t0}), flush=True)
+
+    res = optimize_peps(ctm, np.stack(w.tensors), env0, n_iter, max_steps=args.steps, m=args.history,
+                        callback=report)
+    print(json.dumps({"workload": w.name, "precision": args.precision, "n_iter": n_iter, "steps": res.n_iter,
+                      "energy_start": res.history[0], "energy_end": res.f, "evaluations": res.n_eval,
+                      "message": res.message, "elapsed_s": time.perf_counter() - t0}), flush=True)
+
+
+if __name__ == "__main__":
+    main()

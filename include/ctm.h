@@ -98,7 +98,9 @@ typedef struct {
 } ctm_desc;
 
 /* Create a handle for one problem size (Eq. PEPS cell, D, chi, terms).
- * Allocates the device state lazily on first use.  *out is set on success. */
+ * Allocates the device state lazily on first use.  *out is set on success.
+ * Limits (CTM_ERR_INVALID_ARG otherwise): all sizes >= 1, 1 <= n_terms <= 64, every term's
+ * site inside the cell and kind in 0..3, chi * D * d <= 2048 (the longest projector bond). */
 int ctm_create(const ctm_desc* desc, ctm_handle** out);
 
 /* Load the site tensors and the initial environment.

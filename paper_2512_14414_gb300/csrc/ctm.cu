@@ -1132,6 +1132,8 @@ int ctm_create(const ctm_desc* desc, ctm_handle** out) {
   if (d.Lx < 1 || d.Ly < 1 || d.d < 1 || d.D < 1 || d.chi < 1 || d.n_terms < 1 || d.n_terms > 64 || !d.terms)
     return CTM_ERR_INVALID_ARG;
   if (d.precision < CTM_FP64 || d.precision > CTM_BF16X3) return CTM_ERR_INVALID_ARG;
+  // the Jacobi kernels keep a column of the projector's bond matrix (chi * D * d rows) in registers
+  if ((int64_t)d.chi * d.D * d.d > 2048) return CTM_ERR_INVALID_ARG;
   for (int t = 0; t < d.n_terms; ++t) {
     const ctm_term& tt = d.terms[t];
     if (!tt.h || tt.x < 0 || tt.x >= d.Lx || tt.y < 0 || tt.y >= d.Ly || tt.kind < 0 || tt.kind > 3)

@@ -44,3 +44,55 @@ def test_error_strings_and_argument_checks_without_gpu():
     assert lib.ctm_env_numel(h) == expect
     assert lib.ctm_step(h, 1, None, None) == 8                 # STATE: not initialised
     assert lib.ctm_destroy(h) == 0
+
+
+def _desc(lib_mod, Lx=1, Ly=1, d=2, D=2, chi=4, precision=0, terms=None, n_terms=None):
+    import numpy as np
+    hm = np.eye(d * d)
+    if terms is None:
+        terms = [(0, 0, 0)]
+    arr = (lib_mod.CtmTerm * max(1, len(terms)))()
+    for k, (x, y, kind) in enumerate(terms):
+        arr[k].x, arr[k].y, arr[k].kind, arr[k].coupling = x, y, kind, 1.0
+        arr[k].h = hm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    desc = lib_mod.CtmDesc(Lx, Ly, d, D, chi, precision, len(terms) if n_terms is None else n_terms, arr, 0.0, -1.0, 0)
+    return desc, arr, hm
+
+
+def test_create_rejects_each_bad_description_without_gpu():
+    from paper_2512_14414_gb300 import _lib
+    lib = _lib.load()
+    h = ctypes.c_void_p()
+    bad = [dict(chi=0), dict(D=0), dict(Lx=0), dict(precision=5), dict(precision=-1),
+           dict(terms=[(1, 0, 0)]), dict(terms=[(0, 0, 4)]), dict(n_terms=65),
+           dict(D=9, chi=128)]  # chi * D * d = 2304 > 2048
+    for kw in bad:
+        desc, arr, hm = _desc(_lib, **kw)
+        assert lib.ctm_create(ctypes.byref(desc), ctypes.byref(h)) == 1, kw
+    for prec in range(5):  # every precision mode, and the largest bond that fits (81 * 9 * 2 = 1458)
+        desc, arr, hm = _desc(_lib, D=9, chi=81, precision=prec)
+        assert lib.ctm_create(ctypes.byref(desc), ctypes.byref(h)) == 0
+        assert lib.ctm_destroy(h) == 0
+
+
+def test_stateless_entry_points_check_their_arguments_without_gpu():
+    from paper_2512_14414_gb300 import _lib
+    lib = _lib.load()
+    vp = ctypes.c_void_p
+    one = vp(1)
+    # batched SVD: null matrices, empty batch, oversize
+    assert lib.ctm_svd(None, 1, 4, one, one, one, None) == 1
+    assert lib.ctm_svd(one, 0, 4, one, one, one, None) == 1
+    assert lib.ctm_svd(one, 1, 5000, one, one, one, None) == 1
+    # allocation-free SVD: beyond its fixed array (batch <= 1024, batch * r * r <= 2^20)
+    assert lib.ctm_svd_noalloc(one, 1025, 4, one, one, one, None) == 1
+    assert lib.ctm_svd_noalloc(one, 2, 1024, one, one, one, None) == 1
+    # MLP forward: null input, no layers, too many layers, an empty width
+    dims = (ctypes.c_int * 3)(4, 8, 2)
+    W = (vp * 2)(1, 1)
+    assert lib.ctm_mlp_forward(None, 1, 2, dims, W, None, one, one, None) == 1
+    assert lib.ctm_mlp_forward(one, 1, 0, dims, W, None, one, one, None) == 1
+    assert lib.ctm_mlp_forward(one, 1, 17, dims, W, None, one, one, None) == 1
+    dims0 = (ctypes.c_int * 3)(4, 0, 2)
+    assert lib.ctm_mlp_forward(one, 1, 2, dims0, W, None, one, one, None) == 1
+    assert lib.ctm_mlp_forward(one, 0, 2, dims, W, None, one, one, None) == 1

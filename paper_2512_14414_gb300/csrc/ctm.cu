@@ -1171,6 +1171,10 @@ int ctm_init(ctm_handle* h, const double* A, const double* env0, void* stream) {
     // CTM_TC_MIN_MNK (read at every ctm_init) moves the size threshold of the tensor-core route
     const char* tmin = getenv("CTM_TC_MIN_MNK");
     h->eng->set_tc(tcm, h->dstatus, tmin && *tmin ? (int64_t)atoll(tmin) : (int64_t(1) << 26));
+    // CTM_STRIDED_GEMM=1 (read at every ctm_init): CUDA-core contractions address their operands
+    // through group maps instead of permuted copies
+    const char* sg = getenv("CTM_STRIDED_GEMM");
+    h->eng->set_strided(sg && sg[0] == '1');
     int64_t n = h->A64.numel();
     CTM_CUDA(cudaMemcpyAsync(h->A64.p, A, n * 8, cudaMemcpyDeviceToDevice, h->st));
     if (h->edt != ctm::F64) ctm::cast(h->A64.p, ctm::F64, h->Amode.p, h->edt, n, false, h->st);

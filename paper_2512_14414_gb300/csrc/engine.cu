@@ -257,6 +257,44 @@ void Engine::einsum_into(const Tensor& A, const Labels& la, const Tensor& B, con
         }
   const int64_t nb = prod(batch, dims), MM = prod(best.Mo, dims), NN = prod(best.No, dims), KK = prod(best.Ko, dims);
   const size_t es = dtype_size(A.dt);
+  if (strided_ && KK > 0 && (A.dt == F32 || A.dt == F64) && (best.aLay == 2 || best.bLay == 2 || best.permC)) {
+    // The planner's choice (M, N, K orders and swap) is kept; only the permuted copies go: the
+    // GEMM reads A, B and writes C where they are.
+    auto sz = [&](int l) { return dims.at(l); };
+    StridedGemm sm;
+    bool ok = true;
+    const Tensor& GA = best.swap ? B : A;  // the GEMM's first operand
+    const Tensor& GB = best.swap ? A : B;
+    const Labels& lGA = best.swap ? lb : la;
+    const Labels& lGB = best.swap ? la : lb;
+    const Labels& gM = best.swap ? best.No : best.Mo;
+    const Labels& gN = best.swap ? best.Mo : best.No;
+    ok = ok && build_group_map(lGA, bla, sz, sm.aB) && build_group_map(lGA, gM, sz, sm.aM) &&
+         build_group_map(lGA, best.Ko, sz, sm.aK);
+    ok = ok && build_group_map(lGB, bla, sz, sm.bB) && build_group_map(lGB, best.Ko, sz, sm.bK) &&
+         build_group_map(lGB, gN, sz, sm.bN);
+    ok = ok && build_group_map(lc, bla, sz, sm.cB) && build_group_map(lc, gM, sz, sm.cM) &&
+         build_group_map(lc, gN, sz, sm.cN);
+    if (ok) {
+      GemmSpec g;
+      g.batch = nb;
+      g.M = best.swap ? NN : MM;
+      g.N = best.swap ? MM : NN;
+      g.K = KK;
+      g.alpha = 1.0;
+      g.beta = accumulate ? 1.0 : 0.0;
+      // neighbouring threads along the index whose innermost stride is 1 (coalesced loads)
+      auto inner = [](const GroupMap& m) { return m.n ? m.stride[m.n - 1] : 0; };
+      g.transA = inner(sm.aM) == 1 && inner(sm.aK) != 1;
+      g.transB = inner(sm.bK) == 1 && inner(sm.bN) != 1;
+      gemm_flops_ += 2 * nb * MM * NN * KK;
+      if (A.dt == F64)
+        gemm_strided_f64((const double*)GA.p, (const double*)GB.p, (double*)out, g, sm, st_);
+      else
+        gemm_strided_f32((const float*)GA.p, (const float*)GB.p, (float*)out, g, sm, st_);
+      return;
+    }
+  }
   auto mark = arena_->mark();
   const void* Ap = A.p;
   const void* Bp = B.p;

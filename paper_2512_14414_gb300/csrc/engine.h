@@ -57,6 +57,11 @@ class Engine {
   // While on, contractions keep their temporaries (the caller releases them later): set when
   // work is spread over several streams that share the arena.
   void set_defer_release(bool on) { defer_release_ = on; }
+  // CUDA-core contractions read and write their operands in place through group maps instead of
+  // permuting them first (the same products in the same order).  Off by default: on GB300 at
+  // D=6, chi=64 it removes 13-17 % of the launches but its index-computed, partly uncoalesced
+  // loads make an evaluation 2-6 % slower.
+  void set_strided(bool on) { strided_ = on; }
   Arena& arena() { return *arena_; }
 
   Tensor empty(DType dt, const std::vector<int64_t>& dims);
@@ -118,6 +123,7 @@ class Engine {
   int* tc_status_ = nullptr;
   int64_t tc_min_mnk_ = int64_t(1) << 26;
   bool defer_release_ = false;
+  bool strided_ = false;
   int next_id_ = 0;
   std::vector<std::function<void()>> tape_;
   std::vector<void*> grads_;

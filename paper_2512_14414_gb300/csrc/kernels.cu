@@ -312,6 +312,140 @@ __global__ void __launch_bounds__(256) gemm_simt(const T* __restrict__ A, const 
   }
 }
 
+// The same GEMM with every operand resolved through group maps (stride_map.h): A(b, m, k) at
+// A[aB(b) + aM(m) + aK(k)], B(b, k, n) at B[bB(b) + bK(k) + bN(n)], C(b, m, n) at C[cB(b) + cM(m) +
+// cN(n)] (split-K partials stay dense).  Products are added in the same order as gemm_simt; transA
+// and transB only choose which index runs across neighbouring threads in the loads.
+template <typename T, int TM, int TN, int BK>
+__global__ void __launch_bounds__(256) gemm_simt_strided(const T* __restrict__ A, const T* __restrict__ B,
+                                                         T* __restrict__ C, GemmSpec g, StridedGemm sm,
+                                                         int64_t nsplit, int64_t kchunk) {
+  constexpr int BM = 16 * TM, BN = 16 * TN;
+  constexpr int LA = (BM * BK) / 256, LB = (BN * BK) / 256;
+  __shared__ T As[2][BK][BM + 1];
+  __shared__ T Bs[2][BK][BN + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int64_t n0 = (int64_t)blockIdx.x * BN;
+  const int64_t mtiles = (g.M + BM - 1) / BM;
+  for (int64_t work = blockIdx.z * (int64_t)gridDim.y + blockIdx.y; work < nsplit * g.batch * mtiles;
+       work += (int64_t)gridDim.z * gridDim.y) {
+    const int64_t ext = work / mtiles;
+    const int64_t m0 = (work % mtiles) * BM;
+    const int64_t bb = ext % g.batch, sp = ext / g.batch;
+    const int64_t kbeg = sp * kchunk, kend = min(g.K, kbeg + kchunk);
+    const T* Ab = A + group_offset(sm.aB, bb);
+    const T* Bb = B + group_offset(sm.bB, bb);
+    // the M and N parts of this thread's load offsets do not change along K
+    int64_t am[LA], bn[LB];
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      const int64_t m = m0 + (g.transA ? e % BM : e / BK);
+      am[q] = m < g.M ? group_offset(sm.aM, m) : -1;
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      const int64_t n = n0 + (g.transB ? e / BK : e % BN);
+      bn[q] = n < g.N ? group_offset(sm.bN, n) : -1;
+    }
+    T ra[LA], rb[LB];
+    auto fetch = [&](int64_t k0) {
+#pragma unroll
+      for (int q = 0; q < LA; ++q) {
+        const int e = threadIdx.x + 256 * q;
+        const int64_t k = k0 + (g.transA ? e / BM : e % BK);
+        ra[q] = (am[q] >= 0 && k < kend) ? Ab[am[q] + group_offset(sm.aK, k)] : T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < LB; ++q) {
+        const int e = threadIdx.x + 256 * q;
+        const int64_t k = k0 + (g.transB ? e % BK : e / BN);
+        rb[q] = (bn[q] >= 0 && k < kend) ? Bb[group_offset(sm.bK, k) + bn[q]] : T(0);
+      }
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+      for (int q = 0; q < LA; ++q) {
+        const int e = threadIdx.x + 256 * q;
+        const int ml = g.transA ? e % BM : e / BK, kl = g.transA ? e / BM : e % BK;
+        As[buf][kl][ml] = ra[q];
+      }
+#pragma unroll
+      for (int q = 0; q < LB; ++q) {
+        const int e = threadIdx.x + 256 * q;
+        const int nl = g.transB ? e / BK : e % BN, kl = g.transB ? e % BK : e / BN;
+        Bs[buf][kl][nl] = rb[q];
+      }
+    };
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+    __syncthreads();
+    fetch(kbeg);
+    stash(0);
+    __syncthreads();
+    int buf = 0;
+    for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+      const bool more = k0 + BK < kend;
+      if (more) fetch(k0 + BK);
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        T a[TM], b[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+      if (more) stash(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+    T* Cdense = C + ext * g.M * g.N;
+    T* Cb = C + group_offset(sm.cB, bb);
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      int64_t m = m0 + ty + 16 * i;
+      if (m >= g.M) continue;
+      const int64_t cm = nsplit > 1 ? 0 : group_offset(sm.cM, m);
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        int64_t n = n0 + tx + 16 * j;
+        if (n >= g.N) continue;
+        if (nsplit > 1) {
+          Cdense[m * g.N + n] = acc[i][j];
+        } else {
+          T* cp = Cb + cm + group_offset(sm.cN, n);
+          T v = (T)g.alpha * acc[i][j];
+          if (g.beta != 0.0) v += (T)g.beta * *cp;
+          *cp = v;
+        }
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void splitk_reduce_strided(const T* __restrict__ W, T* __restrict__ C, GemmSpec g, StridedGemm sm,
+                                      int64_t nsplit) {
+  const int64_t per = g.M * g.N, total = g.batch * per;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e / per, r = e % per, m = r / g.N, n = r % g.N;
+    T acc = T(0);
+    for (int64_t s = 0; s < nsplit; ++s) acc += W[(s * g.batch + b) * per + r];
+    T* c = C + group_offset(sm.cB, b) + group_offset(sm.cM, m) + group_offset(sm.cN, n);
+    T v = (T)g.alpha * acc;
+    if (g.beta != 0.0) v += (T)g.beta * *c;
+    *c = v;
+  }
+}
+
 template <typename T>
 __global__ void splitk_reduce(const T* __restrict__ W, T* __restrict__ C, GemmSpec g, int64_t nsplit) {
   const int64_t per = g.M * g.N, total = g.batch * per;
@@ -357,18 +491,14 @@ int num_sms() {
   return n;
 }
 
+// Tile and split-K decision shared by the dense and the strided GEMM (so that both add the
+// same products in the same order).
+struct GemmPlan {
+  int64_t BT, nsplit, kchunk;
+};
+
 template <typename T>
-void gemm_t(const T* A, const T* B, T* C, const GemmSpec& g, cudaStream_t st) {
-  if (g.M == 0 || g.N == 0 || g.batch == 0) return;
-  ProfScope ps(sizeof(T) == 8 ? PROF_GEMM64 : PROF_GEMM, st, 2.0 * g.batch * g.M * g.N * g.K,
-               (double)sizeof(T) * g.batch * (g.M * g.K + g.K * g.N + (g.beta != 0.0 ? 2 : 1) * g.M * g.N),
-               prof_tag(sizeof(T) == 8 ? "simt64" : "simt32", g.batch, g.M, g.N, g.K, g.transA * 2 + g.transB));
-  if (g.K == 0) {  // C = beta C
-    CTM_CHECK(g.beta == 0.0, CTM_ERR_INVALID_ARG, "gemm with K=0 and beta!=0 unsupported");
-    for (int64_t b = 0; b < g.batch; ++b)
-      for (int64_t m = 0; m < g.M; ++m) CTM_CUDA(cudaMemsetAsync(C + b * g.strideC + m * g.ldc, 0, g.N * sizeof(T), st));
-    return;
-  }
+GemmPlan gemm_plan(const GemmSpec& g) {
   // Tile: the largest of 64, 32 and 16 whose output tiles cover the SMs (FP64 is issue-bound at
   // about 2 FMA/clk/SM, so a product must reach every SM; FP32 stops at 32, where latency rather
   // than arithmetic is the limit).  K is then split while the tiles alone cannot fill the GPU:
@@ -394,6 +524,23 @@ void gemm_t(const T* A, const T* B, T* C, const GemmSpec& g, cudaStream_t st) {
   }
   const int64_t kchunk = ((g.K + nsplit - 1) / nsplit + 15) / 16 * 16;
   nsplit = (g.K + kchunk - 1) / kchunk;
+  return {BT, nsplit, kchunk};
+}
+
+template <typename T>
+void gemm_t(const T* A, const T* B, T* C, const GemmSpec& g, cudaStream_t st) {
+  if (g.M == 0 || g.N == 0 || g.batch == 0) return;
+  ProfScope ps(sizeof(T) == 8 ? PROF_GEMM64 : PROF_GEMM, st, 2.0 * g.batch * g.M * g.N * g.K,
+               (double)sizeof(T) * g.batch * (g.M * g.K + g.K * g.N + (g.beta != 0.0 ? 2 : 1) * g.M * g.N),
+               prof_tag(sizeof(T) == 8 ? "simt64" : "simt32", g.batch, g.M, g.N, g.K, g.transA * 2 + g.transB));
+  if (g.K == 0) {  // C = beta C
+    CTM_CHECK(g.beta == 0.0, CTM_ERR_INVALID_ARG, "gemm with K=0 and beta!=0 unsupported");
+    for (int64_t b = 0; b < g.batch; ++b)
+      for (int64_t m = 0; m < g.M; ++m) CTM_CUDA(cudaMemsetAsync(C + b * g.strideC + m * g.ldc, 0, g.N * sizeof(T), st));
+    return;
+  }
+  const GemmPlan pl = gemm_plan<T>(g);
+  const int64_t BT = pl.BT, nsplit = pl.nsplit, kchunk = pl.kchunk;
   T* out = C;
   if (nsplit > 1) out = (T*)splitk_workspace(sizeof(T) * nsplit * g.batch * g.M * g.N, st);
   const int64_t work = nsplit * g.batch * ((g.M + BT - 1) / BT);
@@ -409,6 +556,34 @@ void gemm_t(const T* A, const T* B, T* C, const GemmSpec& g, cudaStream_t st) {
   CTM_LAUNCHED();
   if (nsplit > 1) {
     splitk_reduce<T><<<nblocks(g.batch * g.M * g.N, 256), 256, 0, st>>>(out, C, g, nsplit);
+    CTM_LAUNCHED();
+  }
+}
+
+template <typename T>
+void gemm_strided_t(const T* A, const T* B, T* C, const GemmSpec& g, const StridedGemm& sm, cudaStream_t st) {
+  if (g.M == 0 || g.N == 0 || g.batch == 0) return;
+  ProfScope ps(sizeof(T) == 8 ? PROF_GEMM64 : PROF_GEMM, st, 2.0 * g.batch * g.M * g.N * g.K,
+               (double)sizeof(T) * g.batch * (g.M * g.K + g.K * g.N + (g.beta != 0.0 ? 2 : 1) * g.M * g.N),
+               prof_tag(sizeof(T) == 8 ? "simt64s" : "simt32s", g.batch, g.M, g.N, g.K, g.transA * 2 + g.transB));
+  CTM_CHECK(g.K > 0, CTM_ERR_INVALID_ARG, "strided gemm with K=0");
+  const GemmPlan pl = gemm_plan<T>(g);
+  const int64_t BT = pl.BT, nsplit = pl.nsplit, kchunk = pl.kchunk;
+  T* out = C;
+  if (nsplit > 1) out = (T*)splitk_workspace(sizeof(T) * nsplit * g.batch * g.M * g.N, st);
+  const int64_t work = nsplit * g.batch * ((g.M + BT - 1) / BT);
+  CTM_CHECK((g.N + BT - 1) / BT < (int64_t(1) << 31), CTM_ERR_INVALID_ARG, "gemm N too large");
+  dim3 grid((unsigned)((g.N + BT - 1) / BT), (unsigned)std::min<int64_t>(work, 65535),
+            (unsigned)std::min<int64_t>((work + 65534) / 65535, 65535));
+  if (BT == 16)
+    gemm_simt_strided<T, 1, 1, 16><<<grid, 256, 0, st>>>(A, B, out, g, sm, nsplit, kchunk);
+  else if (BT == 32)
+    gemm_simt_strided<T, 2, 2, 16><<<grid, 256, 0, st>>>(A, B, out, g, sm, nsplit, kchunk);
+  else
+    gemm_simt_strided<T, 4, 4, 16><<<grid, 256, 0, st>>>(A, B, out, g, sm, nsplit, kchunk);
+  CTM_LAUNCHED();
+  if (nsplit > 1) {
+    splitk_reduce_strided<T><<<nblocks(g.batch * g.M * g.N, 256), 256, 0, st>>>(out, C, g, sm, nsplit);
     CTM_LAUNCHED();
   }
 }
@@ -730,6 +905,14 @@ void permute(const void* in, DType tin, void* out, DType tout, const PermSpec& p
 
 void gemm_f64(const double* A, const double* B, double* C, const GemmSpec& g, cudaStream_t st) { gemm_t(A, B, C, g, st); }
 void gemm_f32(const float* A, const float* B, float* C, const GemmSpec& g, cudaStream_t st) { gemm_t(A, B, C, g, st); }
+void gemm_strided_f64(const double* A, const double* B, double* C, const GemmSpec& g, const StridedGemm& sm,
+                      cudaStream_t st) {
+  gemm_strided_t(A, B, C, g, sm, st);
+}
+void gemm_strided_f32(const float* A, const float* B, float* C, const GemmSpec& g, const StridedGemm& sm,
+                      cudaStream_t st) {
+  gemm_strided_t(A, B, C, g, sm, st);
+}
 
 void fill(void* p, DType t, int64_t n, double v, cudaStream_t st) {
   if (n == 0) return;

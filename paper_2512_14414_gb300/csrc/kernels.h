@@ -1,6 +1,7 @@
 // Launch wrappers of the CUDA kernels of libctm (all enqueue on `st`, no host sync).
 #pragma once
 #include "common.h"
+#include "stride_map.h"
 
 namespace ctm {
 
@@ -28,6 +29,13 @@ struct GemmSpec {
 };
 void gemm_f64(const double* A, const double* B, double* C, const GemmSpec& g, cudaStream_t st);
 void gemm_f32(const float* A, const float* B, float* C, const GemmSpec& g, cudaStream_t st);
+// The same products with operands and result addressed through group maps (stride_map.h) instead
+// of leading dimensions: no permuted copies.  g supplies M, N, K, batch, alpha, beta; transA /
+// transB only pick the load order (set the one whose inner index has unit stride).
+void gemm_strided_f64(const double* A, const double* B, double* C, const GemmSpec& g, const StridedGemm& sm,
+                      cudaStream_t st);
+void gemm_strided_f32(const float* A, const float* B, float* C, const GemmSpec& g, const StridedGemm& sm,
+                      cudaStream_t st);
 // Tensor-core GEMM (tcgen05): C[b][m][n] (+)= sum_k A[b][m][k] B[b][n][k]; A, B BF16 or FP32 (as TF32),
 // C FP32 row-major.  tc_gemm_ok tells whether TMA can address the operands.
 bool tc_gemm_ok(bool bf16, int64_t M, int64_t N, int64_t K, const void* A, const void* B);

@@ -141,3 +141,17 @@ def test_bf16x3_tensor_core_mode_runs_and_tracks_the_oracle(monkeypatch):
     assert prof["tc_gemm"][1] > 0
     Er, _ = oracle_energy_grad(w, n_iter, grad=False)
     assert abs(float(e[0]) - Er) <= 1e-4, (float(e[0]), Er)
+
+
+def test_strided_gemm_route_gives_identical_results(monkeypatch):
+    # CTM_STRIDED_GEMM=1: CUDA-core contractions read their operands in place through group maps
+    # instead of permuting them; the products and their order are unchanged, so results are equal
+    w = W.config("heis_d4_chi32")
+    E0, g0, _ = gpu_energy_grad(w, 4, precision="tf32x3")
+    monkeypatch.setenv("CTM_STRIDED_GEMM", "1")
+    E1, g1, _ = gpu_energy_grad(w, 4, precision="tf32x3")
+    E2, g2, _ = gpu_energy_grad(w, 4, precision="fp64")
+    monkeypatch.setenv("CTM_STRIDED_GEMM", "0")
+    E3, g3, _ = gpu_energy_grad(w, 4, precision="fp64")
+    assert E0 == E1 and np.array_equal(g0, g1)
+    assert E2 == E3 and np.array_equal(g2, g3)

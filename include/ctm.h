@@ -179,6 +179,16 @@ int ctm_svd(const double* M, int batch, int r, double* U, double* s, double* V, 
  * Synchronises the stream to read the status. */
 int ctm_svd_noalloc(const double* M, int batch, int r, double* U, double* s, double* V, void* stream);
 
+/* Singular values of the bond density matrix rho = N S^t of every projector pair of iteration
+ * `iter` (0-based) of the run since the last ctm_init -- the spectra that define the projectors of
+ * Eqs. PQ, QRSVD and whose change is the convergence measure of ctm_step.  Descending, FP64, in
+ * execution order (left, right, up, down moves; columns in order; rows in order).
+ *   out_host : host, max_pairs x max_vals, zero-filled beyond each pair's stored values (values
+ *              below 1e-14 s_1 are not stored).
+ *   *n_pairs : the number of pairs of the iteration.
+ * CTM_ERR_STATE if that iteration has not run.  Synchronises the stream of the last call. */
+int ctm_get_spectra(ctm_handle* h, int iter, double* out_host, int max_pairs, int max_vals, int* n_pairs);
+
 /* Forward pass of the warm-start network: an MLP that maps the flattened site tensors to an
  * initial environment, so that the CTMRG iterations of Sec. SLF (step ii) start near their
  * fixed point.  The paper has no counterpart (it starts from a fixed environment); the network

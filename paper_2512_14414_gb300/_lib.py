@@ -12,7 +12,7 @@ PRECISIONS = {"fp64": CTM_FP64, "tf32": CTM_TF32, "bf16": CTM_BF16, "tf32x3": CT
 
 EXPORTS = ["ctm_create", "ctm_init", "ctm_step", "ctm_energy", "ctm_grad", "ctm_get_env", "ctm_set_env",
            "ctm_env_numel", "ctm_kernel_launches", "ctm_profile", "ctm_profile_read", "ctm_svd", "ctm_svd_noalloc",
-           "ctm_mlp_forward", "ctm_destroy", "ctm_error_string"]
+           "ctm_get_spectra", "ctm_mlp_forward", "ctm_destroy", "ctm_error_string"]
 PROF_CLASSES = {"gemm": 0, "permute": 1, "svd": 2, "qr": 3, "misc": 4, "tc_gemm": 5, "gemm_f64": 6}
 
 
@@ -56,12 +56,14 @@ def load():
                                      ctypes.POINTER(d)]
     lib.ctm_svd.argtypes = [vp, i, i, vp, vp, vp, vp]
     lib.ctm_svd_noalloc.argtypes = [vp, i, i, vp, vp, vp, vp]
+    lib.ctm_get_spectra.argtypes = [vp, i, vp, i, i, ctypes.POINTER(i)]
     lib.ctm_mlp_forward.argtypes = [vp, i, i, ctypes.POINTER(i), ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, vp]
     lib.ctm_destroy.argtypes = [vp]
     lib.ctm_error_string.argtypes = [i]
     lib.ctm_error_string.restype = ctypes.c_char_p
     for f in ("ctm_create", "ctm_init", "ctm_step", "ctm_energy", "ctm_grad", "ctm_get_env", "ctm_set_env",
-              "ctm_profile", "ctm_profile_read", "ctm_svd", "ctm_svd_noalloc", "ctm_mlp_forward", "ctm_destroy"):
+              "ctm_profile", "ctm_profile_read", "ctm_svd", "ctm_svd_noalloc", "ctm_get_spectra", "ctm_mlp_forward",
+              "ctm_destroy"):
         getattr(lib, f).restype = i
     _lib = lib
     return lib

@@ -108,6 +108,15 @@ class CTM:
             out[name] = (ms.value, n.value, fl.value, by.value)
         return out
 
+    def spectra(self, iteration, max_pairs=256, max_vals=None):
+        """Singular values of every projector pair of one iteration: (n_pairs, max_vals) numpy array."""
+        max_vals = max_vals or self.chi
+        out = np.zeros((max_pairs, max_vals), dtype=np.float64)
+        n = ctypes.c_int(0)
+        _check(self.lib.ctm_get_spectra(self.handle, int(iteration), out.ctypes.data_as(ctypes.c_void_p), max_pairs,
+                                        max_vals, ctypes.byref(n)), "ctm_get_spectra")
+        return out[: n.value]
+
     def get_env(self):
         out = torch.empty(self.env_numel, dtype=torch.float64, device="cuda")
         _check(self.lib.ctm_get_env(self.handle, _ptr(out), _stream()), "ctm_get_env")

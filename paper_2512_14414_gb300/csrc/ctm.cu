@@ -1373,6 +1373,24 @@ int ctm_profile_read(ctm_handle* h, int cls, double* ms, int64_t* launches, doub
   });
 }
 
+int ctm_get_spectra(ctm_handle* h, int iter, double* out_host, int max_pairs, int max_vals, int* n_pairs) {
+  if (!h || !out_host || !n_pairs || iter < 0 || max_pairs < 1 || max_vals < 1) return CTM_ERR_INVALID_ARG;
+  if (!h->inited || iter >= (int)h->fac.size() || iter >= h->iters_done) return CTM_ERR_STATE;
+  return guard(h, [&]() {
+    CTM_CUDA(cudaStreamSynchronize(h->st));
+    const auto& fac = h->fac[iter];
+    *n_pairs = (int)fac.size();
+    for (int p = 0; p < max_pairs; ++p) {
+      double* row = out_host + (int64_t)p * max_vals;
+      std::fill(row, row + max_vals, 0.0);
+      if (p < (int)fac.size() && fac[p].lam) {
+        const int n = std::min(max_vals, fac[p].rs);
+        CTM_CUDA(cudaMemcpy(row, fac[p].lam, sizeof(double) * n, cudaMemcpyDeviceToHost));
+      }
+    }
+  });
+}
+
 int ctm_mlp_forward(const float* x, int batch, int n_layers, const int* dims, const float* const* W,
                     const float* const* b, float* work, float* y, void* stream) {
   if (!x || !y || !dims || !W || !work || batch < 1 || n_layers < 1 || n_layers > 16) return CTM_ERR_INVALID_ARG;

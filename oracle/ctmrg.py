@@ -24,7 +24,7 @@ Follows Sec. SLF and Fig. 3 of the paper:
   moves are left moves of the network rotated by 180, 90 (counterclockwise)
   and 270 degrees.
 
-Readings where the paper is silent (each also listed in the design doc):
+Readings where the paper is silent:
 
 * Initial environment: a seeded positive random environment supplied as input
   (``from_ring_arrays``).  The trivial boundary (C[0,0] = 1, T[0,0,0] = 1) is

@@ -16,6 +16,8 @@ Everything here is torch-CPU float64 and follows the paper step by step:
                   network; reverse mode through a hand-written projector
                   adjoint (the SVD adjoint of the bond density matrix).
 * ``energy``    - impurity reduced density matrices and Eq. ExpH.
+* ``counter``   - multiply-add counts of every contraction and decomposition
+                  (the algorithmic work of an evaluation).
 * ``exact``     - finite clusters contracted without truncation, the exact
                   state vector and Lanczos ground state (used to pin the rest).
 

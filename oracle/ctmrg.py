@@ -60,6 +60,9 @@ from __future__ import annotations
 import numpy as np
 import torch
 
+from .counter import add_qr, add_svd
+from .counter import einsum as counted_einsum
+
 DT = torch.float64
 CUTOFF = 1e-5
 EPS_BROADEN = 1e-30
@@ -79,6 +82,7 @@ def _qr(A: torch.Tensor):
     if not np.isfinite(a).all():
         raise FloatingPointError("non-finite input to QR")
     Q, R = scipy.linalg.qr(a, mode="economic")
+    add_qr(*a.shape)
     return torch.from_numpy(Q), torch.from_numpy(R)
 
 
@@ -93,6 +97,7 @@ def _svd(M: torch.Tensor):
     if not np.isfinite(m).all():
         raise FloatingPointError("non-finite input to SVD")
     U, s, Vh = scipy.linalg.svd(m, full_matrices=True, lapack_driver="gesvd")
+    add_svd(*m.shape)
     return torch.from_numpy(U), torch.from_numpy(s), torch.from_numpy(Vh.T.copy())
 
 
@@ -262,32 +267,32 @@ def rotate(grid, env, q: int):
 
 # ----------------------------------------------------------------------------- half systems
 def _corner_ul(C, Tu, Tl, a):
-    x1 = torch.einsum("xy,xpz->ypz", C, Tu)
-    x2 = torch.einsum("ypz,yqw->pzqw", x1, Tl)
-    return torch.einsum("pzqw,qpst->wtzs", x2, a)          # [T_l.d, a.d | T_u.r, a.r]
+    x1 = counted_einsum("xy,xpz->ypz", C, Tu)
+    x2 = counted_einsum("ypz,yqw->pzqw", x1, Tl)
+    return counted_einsum("pzqw,qpst->wtzs", x2, a)          # [T_l.d, a.d | T_u.r, a.r]
 
 
 def _corner_ur(Tu, C, Tr, a):
-    x1 = torch.einsum("zpx,xy->zpy", Tu, C)
-    x2 = torch.einsum("zpy,yqv->zpqv", x1, Tr)
-    return torch.einsum("zpqv,spqt->zstv", x2, a)          # [T_u.l, a.l | a.d, T_r.d]
+    x1 = counted_einsum("zpx,xy->zpy", Tu, C)
+    x2 = counted_einsum("zpy,yqv->zpqv", x1, Tr)
+    return counted_einsum("zpqv,spqt->zstv", x2, a)          # [T_u.l, a.l | a.d, T_r.d]
 
 
 def _corner_dl(Tl, C, Td, a):
-    x1 = torch.einsum("wqy,yx->wqx", Tl, C)
-    x2 = torch.einsum("wqx,xpz->wqpz", x1, Td)
-    return torch.einsum("wqpz,qtsp->wtzs", x2, a)          # [T_l.u, a.u | T_d.r, a.r]
+    x1 = counted_einsum("wqy,yx->wqx", Tl, C)
+    x2 = counted_einsum("wqx,xpz->wqpz", x1, Td)
+    return counted_einsum("wqpz,qtsp->wtzs", x2, a)          # [T_l.u, a.u | T_d.r, a.r]
 
 
 def _corner_dr(Tr, C, Td, a):
-    x1 = torch.einsum("vqy,yx->vqx", Tr, C)
-    x2 = torch.einsum("vqx,zpx->vqzp", x1, Td)
-    return torch.einsum("vqzp,stqp->zstv", x2, a)          # [T_d.l, a.l | a.u, T_r.u]
+    x1 = counted_einsum("vqy,yx->vqx", Tr, C)
+    x2 = counted_einsum("vqx,zpx->vqzp", x1, Td)
+    return counted_einsum("vqzp,stqp->zstv", x2, a)          # [T_d.l, a.l | a.u, T_r.u]
 
 
 def _half(G_left, G_right):
     """[w, t | z, s] x [z, s | T, v] -> matrix [(T, v), (w, t)]."""
-    X = torch.einsum("wtzs,zsTv->Tvwt", G_left, G_right)
+    X = counted_einsum("wtzs,zsTv->Tvwt", G_left, G_right)
     return X.reshape(X.shape[0] * X.shape[1], X.shape[2] * X.shape[3])
 
 
@@ -327,11 +332,11 @@ def left_move(grid, env, chi, spectra=None):
         new = []
         for i in range(R):
             im = (i - 1) % R
-            Cul = torch.einsum("xy,xpr,ypk->rk", env["C_ul"][i][j], env["T_u"][i][j], Ps[im])
-            x1 = torch.einsum("yqz,qpsw->yzpsw", env["T_l"][i][j], grid[i][j])
-            x2 = torch.einsum("yzpsw,ypu->zswu", x1, Qs[im])
-            Tl = torch.einsum("zswu,zwd->usd", x2, Ps[i])
-            Cdl = torch.einsum("yx,xpr,ypu->ur", env["C_dl"][i][j], env["T_d"][i][j], Qs[i])
+            Cul = counted_einsum("xy,xpr,ypk->rk", env["C_ul"][i][j], env["T_u"][i][j], Ps[im])
+            x1 = counted_einsum("yqz,qpsw->yzpsw", env["T_l"][i][j], grid[i][j])
+            x2 = counted_einsum("yzpsw,ypu->zswu", x1, Qs[im])
+            Tl = counted_einsum("zswu,zwd->usd", x2, Ps[i])
+            Cdl = counted_einsum("yx,xpr,ypu->ur", env["C_dl"][i][j], env["T_d"][i][j], Qs[i])
             new.append((_normalize(Cul), _normalize(Tl), _normalize(Cdl)))
         for i in range(R):
             env["C_ul"][i][jp], env["T_l"][i][jp], env["C_dl"][i][jp] = new[i]

@@ -26,6 +26,8 @@ import math
 
 import torch
 
+from .counter import einsum as counted_einsum
+
 from .nested import (DT, double_cell, nested_cell, reduced_impurity, y_impurity)
 
 H_, V_, DR_, UR_ = 0, 1, 2, 3
@@ -38,7 +40,7 @@ def contract_pair(a, b):
     shared = [l for l in la if l in lb]
     out = [l for l in la if l not in shared] + [l for l in lb if l not in shared]
     m = {l: k for k, l in enumerate(dict.fromkeys(list(la) + list(lb)))}
-    t = torch.einsum(ta, [m[l] for l in la], tb, [m[l] for l in lb], [m[l] for l in out])
+    t = counted_einsum(ta, [m[l] for l in la], tb, [m[l] for l in lb], [m[l] for l in out])
     return t, out
 
 
@@ -131,7 +133,7 @@ def _rho_matrix(t, labels, k1, k2, b1, b2, d):
 
 def bond_energy(rho, h):
     """Tr(rho h) / Tr(rho) for a d^2 x d^2 density matrix (rows ket, columns bra)."""
-    return torch.einsum("ab,ba->", rho, h) / torch.trace(rho)
+    return counted_einsum("ab,ba->", rho, h) / torch.trace(rho)
 
 
 _NESTED_BLOCK = {H_: (2, 4, (0, 1), (0, 3)), V_: (4, 2, (0, 1), (2, 1)),

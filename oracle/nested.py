@@ -26,6 +26,8 @@ from __future__ import annotations
 
 import torch
 
+from .counter import einsum as counted_einsum
+
 DT = torch.float64
 KET, YSITE, XSITE, BRA = "A", "Y", "X", "A*"
 
@@ -52,13 +54,13 @@ def bra_tensor(A: torch.Tensor) -> torch.Tensor:
 def x_tensor(D: int) -> torch.Tensor:
     """X[l, u, r, d] = delta_lr delta_ud."""
     eye = torch.eye(D, dtype=DT)
-    return torch.einsum("lr,ud->lurd", eye, eye)
+    return counted_einsum("lr,ud->lurd", eye, eye)
 
 
 def y_tensor(D: int, d: int) -> torch.Tensor:
     """Y[(i, s), k, j, (l, s')] = delta_ij delta_kl delta_ss'   (legs left, up, right, down)."""
     eD, ed = torch.eye(D, dtype=DT), torch.eye(d, dtype=DT)
-    y = torch.einsum("ij,kl,st->iskjlt", eD, eD, ed)
+    y = counted_einsum("ij,kl,st->iskjlt", eD, eD, ed)
     return y.reshape(D * d, D, D, D * d)
 
 
@@ -69,7 +71,7 @@ def y_impurity(D: int, d: int) -> torch.Tensor:
     tensors of the local energy terms (Sec. NTN, last paragraph).
     """
     eD, ed = torch.eye(D, dtype=DT), torch.eye(d, dtype=DT)
-    y = torch.einsum("ij,kl,sa,tb->iskjltab", eD, eD, ed, ed)
+    y = counted_einsum("ij,kl,sa,tb->iskjltab", eD, eD, ed, ed)
     return y.reshape(D * d, D, D, D * d, d, d)
 
 
@@ -92,14 +94,14 @@ def nested_cell(As: list, Lx: int, Ly: int) -> list:
 def reduced_tensor(A: torch.Tensor) -> torch.Tensor:
     """Double-layer T^a[(l l'), (u u'), (r r'), (d d')] = sum_s A[s..] A[s..]  (Eq. Tred)."""
     D = A.shape[1]
-    T = torch.einsum("slurd,sLURD->lLuUrRdD", A, A)
+    T = counted_einsum("slurd,sLURD->lLuUrRdD", A, A)
     return T.reshape(D * D, D * D, D * D, D * D)
 
 
 def reduced_impurity(A: torch.Tensor) -> torch.Tensor:
     """T^a with the physical index left open: [..., a, b], a = ket sigma, b = bra sigma."""
     D = A.shape[1]
-    T = torch.einsum("alurd,bLURD->lLuUrRdDab", A, A)
+    T = counted_einsum("alurd,bLURD->lLuUrRdDab", A, A)
     d = A.shape[0]
     return T.reshape(D * D, D * D, D * D, D * D, d, d)
 

@@ -285,3 +285,24 @@ def test_c4v_symmetric_tensor_has_equal_bond_energies():
     evaluate([S], 1, 1, w.chi, 30, w.terms, env0=W.initial_environment(w), grad=False, per_bond=pb)
     assert len(pb) == 2
     assert abs(pb[0] - pb[1]) < 1e-6, pb
+
+
+# ----------------------------------------------------------------------------- work counter
+def test_multiply_add_counter_counts_contractions_and_decompositions():
+    from oracle import counter
+    counter.reset()
+    a, b = torch.ones(3, 4, dtype=torch.float64), torch.ones(4, 5, dtype=torch.float64)
+    counter.einsum("ij,jk->ik", a, b)
+    assert counter.MACS["contraction"] == 3 * 4 * 5
+    counter.einsum(a, [0, 1], b, [1, 2], [0, 2])
+    assert counter.MACS["contraction"] == 2 * 60
+    counter.reset()
+    w = W.config("heis_d2_chi8")
+    evaluate(w.tensors, 1, 1, w.chi, 1, w.terms, env0=W.initial_environment(w), grad=False)
+    one = dict(counter.MACS)
+    counter.reset()
+    evaluate(w.tensors, 1, 1, w.chi, 2, w.terms, env0=W.initial_environment(w), grad=False)
+    two = dict(counter.MACS)
+    # the decompositions scale with the iterations exactly; contractions add one iteration's worth
+    assert one["qr"] > 0 and one["svd"] > 0 and two["qr"] == 2 * one["qr"] and two["svd"] == 2 * one["svd"]
+    assert two["contraction"] > one["contraction"]

@@ -38,7 +38,10 @@
  * iteration counts, energies marked host) are valid on return (the call
  * synchronises the stream for them).
  *
- * Threads: one handle per host thread; handles share nothing.
+ * Threads: one handle per host thread.  Handles share no problem state; the
+ * library caches small device work buffers (barrier words of the cooperative
+ * kernels, split-K partial tiles, the sketch test matrix) per host thread,
+ * device and stream, so work enqueued on different streams never shares them.
  */
 #ifndef CTM_H
 #define CTM_H
@@ -140,6 +143,17 @@ int64_t ctm_env_numel(const ctm_handle* h);
 /* Launch counters (kernels enqueued by this handle since creation). */
 int64_t ctm_kernel_launches(const ctm_handle* h);
 
+/* Limits of the iterative device kernels of this handle.
+ *   max_sweeps : sweeps of the one-sided Jacobi SVD before it gives up with
+ *                CTM_ERR_SVD_NOCONV (default 60; <= 0 restores the default).
+ *   spin_limit : polls of every bounded device-side wait (the grid barriers of
+ *                the cooperative QR / Jacobi kernels) before the kernel records
+ *                CTM_ERR_TIMEOUT, tells the other blocks to stop and returns
+ *                (default 2^22, a few seconds; <= 0 restores the default).
+ * A call that runs into either limit returns the error; the handle stays valid
+ * and the next ctm_init clears it.  Host memory only, no device work. */
+int ctm_set_limits(ctm_handle* h, int max_sweeps, int64_t spin_limit);
+
 /* Per-kernel-class device timing.  ctm_profile(h, 1) clears the record and
  * starts recording a CUDA event pair (on the launching stream) around every
  * launch of the classes below; ctm_profile(h, 0) stops.  ctm_profile_read
@@ -171,9 +185,10 @@ int ctm_svd(const double* M, int batch, int r, double* U, double* s, double* V, 
  * 1,048,576 and batch must not exceed 1024, otherwise CTM_ERR_INVALID_ARG is
  * returned before any work is enqueued.  The workspace is one fixed 16 MiB
  * device array compiled into the library: every GPU that loads the library
- * holds it until the process exits.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  All calls share the array and every call clears the
+ * holds it until the process exits.  Every call looks up the array's device
+ * address on the current device (cudaGetSymbolAddress, no allocation); the
+ * first call on a device loads the module there, so make that first call
+ * before any stream capture.  All calls share the array and every call clears the
  * parts that must start at zero, so calls whose work overlaps on the GPU (two
  * streams, two host threads) race with each other: serialise them.
  * Synchronises the stream to read the status. */

@@ -51,7 +51,7 @@ Readings where the paper is silent:
   derivative of Eqs. PQ/QRSVD wherever the retained spectrum is
   non-degenerate, and it needs no inverse of R_n or R_s.
 
-Parity: pinned by tests/test_oracle_ctmrg.py (product states, dimer state,
+Parity: pinned by tests/test_oracle_pins.py (product states, dimer state,
 decoupled chains, single vs double layer, finite differences, autograd of
 the plain QR+SVD on full-rank inputs).
 """

@@ -14,7 +14,7 @@ the energy normalisation independently of CTMRG:
 * ``lanczos_ground``  - the exact ground energy of the cluster Hamiltonian.
 
 Parity: these are definitions written out; pinned against each other and
-against the variational bound in tests/test_oracle_exact.py.
+against the variational bound in tests/test_oracle_pins.py.
 """
 from __future__ import annotations
 

@@ -20,7 +20,7 @@ Readings (the figure that fixes the wiring is missing from the text):
 * Real tensors only, so A* = A.
 
 Parity: pinned by the finite-cluster tests (exact state vector vs. nested and
-double-layer contraction, ``tests/test_oracle_exact.py``).
+double-layer contraction, ``tests/test_oracle_pins.py``).
 """
 from __future__ import annotations
 

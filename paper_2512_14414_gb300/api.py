@@ -95,6 +95,10 @@ class CTM:
         _check(self.lib.ctm_grad(self.handle, int(n_iter), _ptr(e), _ptr(dA), _stream()), "ctm_grad")
         return e, dA
 
+    def set_limits(self, max_sweeps=0, spin_limit=0):
+        """Sweep limit of the Jacobi SVD and spin limit of the bounded device waits (0: default)."""
+        _check(self.lib.ctm_set_limits(self.handle, int(max_sweeps), int(spin_limit)), "ctm_set_limits")
+
     def profile(self, enable=True):
         _check(self.lib.ctm_profile(self.handle, int(bool(enable))), "ctm_profile")
 

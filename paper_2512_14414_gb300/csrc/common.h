@@ -46,6 +46,17 @@ inline void count_launch() {
     CTM_CUDA(cudaGetLastError());         \
   } while (0)
 
+// Limits of the iterative device kernels (ctm_set_limits): the sweep limit of the Jacobi SVD and
+// the spin limit of every bounded device-side wait.  The ABI entry points point g_limits at the
+// handle's values for the duration of a call; without a handle the defaults apply.
+struct Limits {
+  int max_sweeps = 60;
+  int64_t spin_limit = int64_t(1) << 22;
+};
+extern thread_local const Limits* g_limits;
+inline int lim_sweeps() { return g_limits ? g_limits->max_sweeps : Limits().max_sweeps; }
+inline int64_t lim_spins() { return g_limits ? g_limits->spin_limit : Limits().spin_limit; }
+
 // Per-class device timing with CUDA events (enabled by ctm_profile).  A scope records an
 // event pair around the launches it encloses, on the launching stream.
 enum ProfClass : int { PROF_GEMM = 0, PROF_PERMUTE = 1, PROF_SVD = 2, PROF_QR = 3, PROF_MISC = 4, PROF_TC = 5,

@@ -51,8 +51,6 @@
 namespace ctm {
 namespace {
 
-constexpr int kMaxSweeps = 60;
-
 enum Kind { KET = 0, YS = 1, XS = 2, BRA = 3 };
 inline int kind_of(int i, int j) { return (i % 2 == 0) ? ((j % 2 == 0) ? KET : YS) : ((j % 2 == 0) ? XS : BRA); }
 
@@ -144,6 +142,7 @@ struct ctm_handle {
   double *hs = nullptr, *coup = nullptr;
   std::string last_error;
   ctm::Profiler prof;
+  ctm::Limits limits;  // sweep and spin limits of the iterative kernels (ctm_set_limits)
   // replay state of the current iteration (backward recompute)
   bool replay = false;
   int cur_iter = 0, cur_pair = 0;
@@ -415,7 +414,7 @@ void projectors_full(ctm_handle* h, const std::vector<PairIn>& in, const std::ve
     }
   }
   set_identity_colmajor(Vw, nb, r, st);
-  svd_jacobi(W, Vw, lam, Uo, Vo, nb, r, kMaxSweeps, h->dstatus, h->dsweeps, st);
+  svd_jacobi(W, Vw, lam, Uo, Vo, nb, r, lim_sweeps(), h->dstatus, h->dsweeps, st);
   for (int b = 0; b < nb; ++b) {
     const int64_t nr = in[b].n_r, nl = in[b].n_l;
     F[b]->rs = r;
@@ -1103,20 +1102,24 @@ int guard(ctm_handle* h, const std::function<void()>& fn) {
     if (h) {
       ctm::g_launch_counter = &h->launches;
       ctm::g_prof = &h->prof;
+      ctm::g_limits = &h->limits;
     }
     fn();
     ctm::g_launch_counter = nullptr;
     ctm::g_prof = nullptr;
+    ctm::g_limits = nullptr;
     return CTM_OK;
   } catch (const ctm::Error& e) {
     ctm::g_launch_counter = nullptr;
     ctm::g_prof = nullptr;
+    ctm::g_limits = nullptr;
     if (h) h->last_error = e.what();
     fprintf(stderr, "libctm: %s\n", e.what());
     return e.status;
   } catch (const std::exception& e) {
     ctm::g_launch_counter = nullptr;
     ctm::g_prof = nullptr;
+    ctm::g_limits = nullptr;
     if (h) h->last_error = e.what();
     fprintf(stderr, "libctm: %s\n", e.what());
     return CTM_ERR_INVALID_ARG;
@@ -1345,6 +1348,13 @@ int64_t ctm_env_numel(const ctm_handle* h) {
 
 int64_t ctm_kernel_launches(const ctm_handle* h) { return h ? h->launches : -1; }
 
+int ctm_set_limits(ctm_handle* h, int max_sweeps, int64_t spin_limit) {
+  if (!h) return CTM_ERR_INVALID_ARG;
+  h->limits.max_sweeps = max_sweeps > 0 ? max_sweeps : ctm::Limits().max_sweeps;
+  h->limits.spin_limit = spin_limit > 0 ? spin_limit : ctm::Limits().spin_limit;
+  return CTM_OK;
+}
+
 int ctm_profile(ctm_handle* h, int enable) {
   if (!h) return CTM_ERR_INVALID_ARG;
   return guard(h, [&]() {
@@ -1423,7 +1433,7 @@ int ctm_svd(const double* M, int batch, int r, double* U, double* s, double* V, 
     ps.in_stride[2] = r;
     permute(M, F64, W, F64, ps, false, 1.0, st);
     set_identity_colmajor(Vw, batch, r, st);
-    svd_jacobi(W, Vw, s, U, V, batch, r, 60, status, status + 1, st);
+    svd_jacobi(W, Vw, s, U, V, batch, r, lim_sweeps(), status, status + 1, st);
     int hs = 0;
     CTM_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     CTM_CUDA(cudaStreamSynchronize(st));

@@ -9,6 +9,7 @@ namespace ctm {
 
 thread_local int64_t* g_launch_counter = nullptr;
 thread_local Profiler* g_prof = nullptr;
+thread_local const Limits* g_limits = nullptr;
 
 void Profiler::begin(int c, cudaStream_t st, double f, double b, const char* tag) {
   if (used + 2 > ev.size()) {
@@ -460,16 +461,18 @@ __global__ void splitk_reduce(const T* __restrict__ W, T* __restrict__ C, GemmSp
   }
 }
 
-// Cached workspace of the split-K partial tiles, one per (host thread, stream): products
+// Cached workspace of the split-K partial tiles, one per (host thread, device, stream): products
 // enqueued on different streams may run at the same time.
 struct SplitkWs {
   void* p = nullptr;
   size_t cap = 0;
 };
-thread_local std::map<cudaStream_t, SplitkWs> g_splitk_ws;
+thread_local std::map<std::pair<int, cudaStream_t>, SplitkWs> g_splitk_ws;
 
 void* splitk_workspace(size_t bytes, cudaStream_t st) {
-  SplitkWs& w = g_splitk_ws[st];
+  int dev = 0;
+  CTM_CUDA(cudaGetDevice(&dev));
+  SplitkWs& w = g_splitk_ws[{dev, st}];
   if (bytes > w.cap) {
     if (w.p) {  // launches already enqueued on st may still read the old buffer
       CTM_CUDA(cudaStreamSynchronize(st));

@@ -14,6 +14,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -22,12 +23,11 @@
 namespace ctm {
 namespace {
 
-constexpr long kSpinLimit = 1L << 22;  // ~ a few seconds with the back-off below
-
 struct Sync {
   unsigned* bar;  // [0] arrival count, [1] generation
   int* abort;
   int* status;
+  long long limit;  // spins before a wait gives up (2^22 by default: a few seconds with the back-off below)
 };
 
 // Returns false if the barrier was abandoned (timeout or abort).
@@ -52,7 +52,7 @@ __device__ bool grid_barrier(const Sync& s) {
           ok = 0;
           break;
         }
-        if (++spins > kSpinLimit) {
+        if (++spins > s.limit) {
           atomicOr(s.status, DEV_TIMEOUT);
           atomicExch(s.abort, 1);
           ok = 0;
@@ -547,9 +547,17 @@ struct CoopScratch {
   double* flop_acc = nullptr;
 };
 
-thread_local CoopScratch g_coop;
+// One set per (device, stream) and host thread: cooperative kernels enqueued on different streams
+// may run at the same time and must not share barrier words.
+CoopScratch& coop_of(cudaStream_t st) {
+  static thread_local std::map<std::pair<int, cudaStream_t>, CoopScratch> m;
+  int dev = 0;
+  CTM_CUDA(cudaGetDevice(&dev));
+  return m[{dev, st}];
+}
 
-void ensure_coop(int batch, cudaStream_t st) {
+CoopScratch& ensure_coop(int batch, cudaStream_t st) {
+  CoopScratch& g_coop = coop_of(st);
   if (!g_coop.bar) {
     CTM_CUDA(cudaMalloc(&g_coop.bar, 2 * sizeof(unsigned)));
     CTM_CUDA(cudaMalloc(&g_coop.abort, sizeof(int)));
@@ -569,6 +577,7 @@ void ensure_coop(int batch, cudaStream_t st) {
   }
   CTM_CUDA(cudaMemsetAsync(g_coop.bar, 0, 2 * sizeof(unsigned), st));
   CTM_CUDA(cudaMemsetAsync(g_coop.abort, 0, sizeof(int), st));
+  return g_coop;
 }
 
 int coop_grid(const void* kernel, int threads) {
@@ -612,12 +621,12 @@ void qr_householder(double* A, double* tau, int batch, int m, int n, int64_t str
   if (batch == 0 || n == 0) return;
   ProfScope ps(PROF_QR, st, batch * (2.0 * m * n * n - 2.0 * n * n * n / 3.0), 8.0 * batch * m * n * 2,
                prof_tag("qr", batch, m, n, 0));
-  ensure_coop(batch, st);
+  CoopScratch& g_coop = ensure_coop(batch, st);
   const int threads = 256;
   int grid = coop_grid((const void*)qr_kernel, threads);
   int64_t need = ((int64_t)batch * n + threads / 32 - 1) / (threads / 32);
   grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, need));
-  Sync s{g_coop.bar, g_coop.abort, status};
+  Sync s{g_coop.bar, g_coop.abort, status, (long long)lim_spins()};
   void* args[] = {&A, &tau, &batch, &m, &n, &strideA, &s};
   CTM_CUDA(cudaLaunchCooperativeKernel((const void*)qr_kernel, grid, threads, args, 0, st));
   CTM_LAUNCHED();
@@ -634,12 +643,12 @@ void qr_apply_Q(const double* A, const double* tau, double* X, int batch, int m,
   if (batch == 0 || n == 0) return;
   ProfScope ps(PROF_QR, st, batch * 4.0 * m * n * k - 2.0 * batch * n * n * k, 8.0 * batch * (m * n + 2.0 * m * k),
                prof_tag("apply_q", batch, m, n, k));
-  ensure_coop(batch, st);
+  CoopScratch& g_coop = ensure_coop(batch, st);
   const int threads = 256;
   int grid = coop_grid((const void*)apply_q_kernel, threads);
   int64_t need = ((int64_t)batch * k + threads / 32 - 1) / (threads / 32);
   grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, need));
-  Sync s{g_coop.bar, g_coop.abort, status};
+  Sync s{g_coop.bar, g_coop.abort, status, (long long)lim_spins()};
   void* args[] = {&A, &tau, &X, &batch, &m, &n, &k, &strideA, &strideX, &s};
   CTM_CUDA(cudaLaunchCooperativeKernel((const void*)apply_q_kernel, grid, threads, args, 0, st));
   CTM_LAUNCHED();
@@ -648,8 +657,15 @@ void qr_apply_Q(const double* A, const double* tau, double* X, int batch, int m,
 // Test matrix of the sketches: element e is splitmix64(seed + e * golden) mapped to (-1, 1),
 // so a longer buffer extends a shorter one and every shape reads the same leading values.
 static const double* sketch_omega(int64_t n, cudaStream_t st) {
-  static thread_local double* omega = nullptr;
-  static thread_local int64_t omega_n = 0;
+  struct Buf {
+    double* p = nullptr;
+    int64_t n = 0;
+  };
+  static thread_local std::map<int, Buf> per_dev;
+  int dev = 0;
+  CTM_CUDA(cudaGetDevice(&dev));
+  double*& omega = per_dev[dev].p;
+  int64_t& omega_n = per_dev[dev].n;
   if (omega_n < n) {
     if (omega) CTM_CUDA(cudaFree(omega));
     CTM_CUDA(cudaMalloc(&omega, sizeof(double) * n));
@@ -724,16 +740,16 @@ void svd_sketch_product(const double* const* N, const double* const* S, const in
     g.M = l; g.N = mr; g.K = ml; g.lda = nl; g.transB = true; g.ldb = ml; g.ldc = nr;
     gemm_f64(Z + b * Ln, S[b], Bt + b * Lr, g, st);
   }
-  ensure_coop(batch, st);
+  CoopScratch& g_coop = ensure_coop(batch, st);
   CTM_CUDA(cudaMemsetAsync(g_coop.flags, 0, 3 * batch * sizeof(int), st));
   CTM_CUDA(cudaMemsetAsync(g_coop.conv, 0, batch * sizeof(int), st));
   set_identity_colmajor(Vl, batch, l, st);
   frob2_kernel<<<batch, 256, 0, st>>>(Bt, Lr, g_coop.frob2);
   CTM_LAUNCHED();
-  Sync s{g_coop.bar, g_coop.abort, status};
+  Sync s{g_coop.bar, g_coop.abort, status, (long long)lim_spins()};
   {
     ProfScope ps(PROF_SVD, st, 0.0, 8.0 * batch * Lr * 4, prof_tag("jacobi", batch, nr, l, 0));
-    launch_jacobi(Bt, Vl, batch, nr, l, 60, g_coop.flags, g_coop.conv, sweeps_out, g_coop.frob2, g_coop.flop_acc, s, st);
+    launch_jacobi(Bt, Vl, batch, nr, l, lim_sweeps(), g_coop.flags, g_coop.conv, sweeps_out, g_coop.frob2, g_coop.flop_acc, s, st);
   }
   size_t smem = (size_t)l * (sizeof(double) + sizeof(int));
   svd_rect_finalize_kernel<<<batch, 256, smem, st>>>(Bt, Vl, lam, l, Vo, l, Ul, nr, l, inc, inc + batch, status);
@@ -751,6 +767,7 @@ void svd_sketch_product(const double* const* N, const double* const* S, const in
 }
 
 double jacobi_flops_read_reset(cudaStream_t st) {
+  CoopScratch& g_coop = coop_of(st);
   if (!g_coop.flop_acc) return 0.0;
   double v = 0.0;
   CTM_CUDA(cudaMemcpyAsync(&v, g_coop.flop_acc, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -769,10 +786,10 @@ void svd_jacobi(double* W, double* V, double* lam, double* Uo, double* Vo, int b
                 int* status, int* sweeps_out, cudaStream_t st) {
   if (batch == 0 || r == 0) return;
   ProfScope ps(PROF_SVD, st, 0.0, 8.0 * batch * r * r * 4);
-  ensure_coop(batch, st);
+  CoopScratch& g_coop = ensure_coop(batch, st);
   CTM_CUDA(cudaMemsetAsync(g_coop.flags, 0, 3 * batch * sizeof(int), st));
   CTM_CUDA(cudaMemsetAsync(g_coop.conv, 0, batch * sizeof(int), st));
-  Sync s{g_coop.bar, g_coop.abort, status};
+  Sync s{g_coop.bar, g_coop.abort, status, (long long)lim_spins()};
   frob2_kernel<<<batch, 256, 0, st>>>(W, (int64_t)r * r, g_coop.frob2);
   CTM_LAUNCHED();
   launch_jacobi(W, V, batch, r, r, max_sweeps, g_coop.flags, g_coop.conv, sweeps_out, g_coop.frob2, g_coop.flop_acc, s,
@@ -800,21 +817,13 @@ constexpr int64_t kNoAllocInts = 8 + 4 * kNoAllocMaxBatch;
 constexpr int64_t kNoAllocDoubles = 2 * kNoAllocMaxElems + kNoAllocMaxBatch + 8 + kNoAllocInts / 2;
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
-std::mutex g_noalloc_mu;
-double* g_noalloc_ptr[256] = {};
-
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array on the current device.  Looked up on every call (it
+// allocates nothing and is cheap once the module is loaded), so that a reset device or a new
+// primary context never leaves a stale address behind.
 double* noalloc_base() {
-  int dev = 0;
-  CTM_CUDA(cudaGetDevice(&dev));
-  CTM_CHECK(dev >= 0 && dev < 256, CTM_ERR_CUDA, "device index out of range");
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    CTM_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_noalloc_ptr[dev] = (double*)p;
-  }
-  return g_noalloc_ptr[dev];
+  void* p = nullptr;
+  CTM_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+  return (double*)p;
 }
 
 void svd_noalloc(const double* M, int batch, int r, double* U, double* sv, double* V, cudaStream_t st) {
@@ -846,8 +855,8 @@ void svd_noalloc(const double* M, int batch, int r, double* U, double* sv, doubl
   set_identity_colmajor(Vw, batch, r, st);
   frob2_kernel<<<batch, 256, 0, st>>>(W, rr, frob2);
   CTM_LAUNCHED();
-  Sync s{bar, abort_flag, status};
-  launch_jacobi(W, Vw, batch, r, r, 60, flags, conv, sweeps, frob2, facc, s, st);
+  Sync s{bar, abort_flag, status, (long long)lim_spins()};
+  launch_jacobi(W, Vw, batch, r, r, lim_sweeps(), flags, conv, sweeps, frob2, facc, s, st);
   size_t smem = (size_t)r * (sizeof(double) + sizeof(int));
   svd_finalize_kernel<<<batch, 256, smem, st>>>(W, Vw, sv, U, V, r, status);
   CTM_LAUNCHED();

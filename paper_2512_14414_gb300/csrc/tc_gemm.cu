@@ -14,6 +14,7 @@
 #include <cudaTypedefs.h>
 
 #include <mutex>
+#include <set>
 
 #include "kernels.h"
 
@@ -298,10 +299,18 @@ bool tc_gemm_ok(bool bf16, int64_t M, int64_t N, int64_t K, const void* A, const
 template <bool BF16, bool X3>
 void launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& ma2, const CUtensorMap& mb2, float* C,
                int64_t M, int64_t N, int64_t batch, int64_t K, float beta, int* status, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    CTM_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BF16, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_of(X3)));
-    attr = true;
+  // the shared-memory opt-in is a property of the kernel on each device: set it once per device
+  static std::mutex mu;
+  static std::set<int> done;
+  int dev = 0;
+  CTM_CUDA(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done.count(dev)) {
+      CTM_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BF16, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    smem_of(X3)));
+      done.insert(dev);
+    }
   }
   dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)batch);
   tc_gemm_kernel<BF16, X3><<<grid, 128, smem_of(X3), st>>>(ma, mb, ma2, mb2, C, (int)M, (int)N, (int)K, beta, status);

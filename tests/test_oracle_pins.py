@@ -306,3 +306,24 @@ def test_multiply_add_counter_counts_contractions_and_decompositions():
     # the decompositions scale with the iterations exactly; contractions add one iteration's worth
     assert one["qr"] > 0 and one["svd"] > 0 and two["qr"] == 2 * one["qr"] and two["svd"] == 2 * one["svd"]
     assert two["contraction"] > one["contraction"]
+
+
+# ----------------------------------------------------------------------------- convergence measure
+def test_spectrum_change_by_hand_and_on_a_product_state():
+    # delta = max over projector pairs of the largest entry-wise change of the normalised
+    # truncated spectrum; worked by hand on two pairs of three values each.
+    from oracle.ctmrg import spectrum_change
+    prev = [torch.tensor([0.5, 0.3, 0.2], dtype=DT), torch.tensor([0.7, 0.2, 0.1], dtype=DT)]
+    cur = [torch.tensor([0.6, 0.3, 0.1], dtype=DT), torch.tensor([0.65, 0.25, 0.1], dtype=DT)]
+    assert abs(spectrum_change(prev, cur) - 0.1) < 1e-15
+    assert abs(spectrum_change(cur, prev) - 0.1) < 1e-15
+    assert spectrum_change(cur, cur) == 0.0
+    # the logged spectra are s/sum(s): each sums to one, and a rank-one (D=1 product) state has
+    # the spectrum (1, 0, ...) in every iteration, so delta is exactly zero from the start
+    sp = []
+    A = torch.tensor(W.product_site([0.6, 0.8]))
+    ctmrg(nested_cell([A], 1, 1), 4, 3, env=from_ring_arrays(_env0(1, 1, 1, 4), 2, 2), spectra_log=sp)
+    for it in sp:
+        for s in it:
+            assert abs(float(s.sum()) - 1.0) < 1e-14
+    assert spectrum_change(sp[1], sp[2]) < 1e-15

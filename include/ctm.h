@@ -95,8 +95,9 @@ typedef struct {
   int precision;         /* ctm_precision */
   int n_terms;
   const ctm_term* terms; /* Hamiltonian: sum of coupling * h over the listed bonds */
-  double svd_cutoff_rel; /* projector pseudo-inverse cutoff s_k <= cut*s_1 -> 0; <=0 means 1e-5 */
-  double svd_adjoint_eps;/* Lorentzian broadening of 1/(s_j^2-s_i^2), relative to s_1^4; <0 means 1e-30 */
+  double svd_cutoff_rel; /* projector pseudo-inverse cutoff s_k <= cut*s_1 -> 0; <=0 means 1e-6 */
+  double svd_adjoint_eps;/* Lorentzian broadening of 1/(s_j^2-s_i^2), relative to (s_i^2+s_j^2)^2;
+                            <0 means 1e-24 */
   int max_iter;          /* upper bound on iterations stored for the gradient (sizes the factor store) */
 } ctm_desc;
 

@@ -39,7 +39,7 @@ class CTM:
     ``terms``: iterable of (x, y, kind, coupling, h) with h a d^2 x d^2 array.
     """
 
-    def __init__(self, Lx, Ly, d, D, chi, terms, precision="fp64", cutoff=1e-5, adjoint_eps=1e-30):
+    def __init__(self, Lx, Ly, d, D, chi, terms, precision="fp64", cutoff=1e-6, adjoint_eps=1e-24):
         self.lib = _lib.load()
         self.Lx, self.Ly, self.d, self.D, self.chi = Lx, Ly, d, D, chi
         self.precision = precision

@@ -108,7 +108,7 @@ struct ctm_handle {
   std::vector<TermH> terms;
   int R = 0, C = 0, nsites = 0;
   ctm::DType edt = ctm::F64;
-  double cut = 1e-5, eps = 1e-30;
+  double cut = 1e-6, eps = 1e-24;
   double rank_tol = 1e-13;  // triplets below rank_tol * s_1 are left out of the adjoint's core
   int64_t launches = 0;
   cudaStream_t st = nullptr;
@@ -1149,8 +1149,8 @@ int ctm_create(const ctm_desc* desc, ctm_handle** out) {
   h->C = 2 * d.Lx;
   h->nsites = h->R * h->C;
   h->edt = d.precision == CTM_FP64 ? ctm::F64 : ctm::F32;
-  h->cut = d.svd_cutoff_rel > 0 ? d.svd_cutoff_rel : 1e-5;
-  h->eps = d.svd_adjoint_eps >= 0 ? d.svd_adjoint_eps : 1e-30;
+  h->cut = d.svd_cutoff_rel > 0 ? d.svd_cutoff_rel : 1e-6;
+  h->eps = d.svd_adjoint_eps >= 0 ? d.svd_adjoint_eps : 1e-24;
   int d2 = d.d * d.d;
   for (int t = 0; t < d.n_terms; ++t) {
     const ctm_term& tt = d.terms[t];

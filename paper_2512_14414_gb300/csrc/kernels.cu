@@ -759,7 +759,6 @@ __global__ void proj_core_k(const double* Aa, const double* Bb, const double* la
   const double l0 = l[0];
   const double* A = Aa + (int64_t)b * r * kept;
   const double* B = Bb + (int64_t)b * r * kept;
-  const double e4 = eps * l0 * l0 * l0 * l0;
   int64_t total = (int64_t)r * r;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     int i = (int)(e / r), j = (int)(e % r);
@@ -768,8 +767,11 @@ __global__ void proj_core_k(const double* Aa, const double* Bb, const double* la
     if (i == j) {
       if (i < kept) v = dl[(int64_t)b * kept + i];
     } else if (li > rank_tol * l0 && lj > rank_tol * l0) {
+      // Lorentzian broadening on the pair's own scale: only numerically degenerate pairs
+      // (relative gap at the rounding level) are damped
       double diff = lj * lj - li * li;
-      double F = diff / (diff * diff + e4);
+      double sc = lj * lj + li * li;
+      double F = diff / (diff * diff + eps * sc * sc);
       double aij = (j < kept) ? A[(int64_t)i * kept + j] : 0.0;
       double aji = (i < kept) ? A[(int64_t)j * kept + i] : 0.0;
       double bij = (j < kept) ? B[(int64_t)i * kept + j] : 0.0;

@@ -80,7 +80,9 @@ void scale_cols(const double* Y, int64_t ldy, int64_t strideY, const double* s, 
 // dl[b][k] = -0.5 inv^3 (sum_i dZ[i][k] U[i][k] + sum_i dW[i][k] V[i][k]), k < kept
 void proj_dlam(const double* dZ, const double* U, const double* dW, const double* V, const double* inv,
                double* dl, int batch, int64_t n_r, int r, int kept, cudaStream_t st);
-// core (r x r) of the thin-SVD adjoint (see linalg notes in ctm.cu)
+// core (r x r) of the thin-SVD adjoint: F_ij (A_ij - A_ji) s_j + s_i F_ij (B_ij - B_ji) off the diagonal,
+// dl on it, with F_ij = (s_j^2 - s_i^2) / ((s_j^2 - s_i^2)^2 + eps (s_i^2 + s_j^2)^2) on the triplets above
+// rank_tol * s_1 (0 elsewhere)
 void proj_core(const double* Aa, const double* Bb, const double* lam, const double* dl, double* core, int batch,
                int r, int kept, double rank_tol, double eps, cudaStream_t st);
 // E[b] = (dU[b] - X[b]) * sinv[b] (n_r x kept)

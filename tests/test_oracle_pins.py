@@ -225,7 +225,10 @@ def test_gradient_matches_central_finite_differences():
         Ep, _ = evaluate([A + h * v], 1, 1, w.chi, n_it, w.terms, env0=env0, grad=False)
         Em, _ = evaluate([A - h * v], 1, 1, w.chi, n_it, w.terms, env0=env0, grad=False)
         fd = (Ep - Em) / (2 * h)
-        assert abs(fd - (g[0] * v).sum()) < 1e-7 * max(1e-3, abs(fd)) + 1e-9
+        # central differences at this step agree with smaller steps to ~1e-8 of |dE/dA| on these
+        # inputs; the bar (relative to the gradient norm, v being a unit vector) sits above that
+        # and well below the 1e-5 parity bar of the GPU gradient
+        assert abs(fd - (g[0] * v).sum()) < 1e-6 * np.linalg.norm(g[0])
 
 
 def test_scale_invariance_and_euler_relation():
@@ -327,3 +330,45 @@ def test_spectrum_change_by_hand_and_on_a_product_state():
         for s in it:
             assert abs(float(s.sum()) - 1.0) < 1e-14
     assert spectrum_change(sp[1], sp[2]) < 1e-15
+
+
+def test_sign_mixed_random_tensors_do_not_converge_but_the_workload_inputs_do():
+    # Why the workloads are not pure N(0, 1/(2 D^4)) draws: on such a tensor the nested CTMRG
+    # with chi = 8 never settles -- the energy after n iterations jumps by O(1) from one n to the
+    # next (one draw shown; D=4 and D=6, chi=64 behave the same) -- whereas the correlated core
+    # plus eta = 0.2 Gaussian noise of the workloads converges.
+    D, chi = 2, 8
+    signed = np.random.default_rng(1).standard_normal((2, D, D, D, D)) / np.sqrt(2 * D**4)
+    terms = W.heisenberg_terms_rotated()
+    env0 = _env0(1, 1, D, chi)
+    for A, lo, hi in ((signed, 0.1, np.inf), (W.noisy_ising_site(1, 2, D), 0.0, 1e-5)):
+        Es = [evaluate([A], 1, 1, chi, n, terms, env0=env0, grad=False)[0] for n in (14, 16, 18, 20)]
+        spread = max(Es) - min(Es)
+        assert lo <= spread < hi, (Es, spread)
+
+
+def test_gradient_does_not_depend_on_the_svd_algorithm_at_the_cutoff():
+    # The pseudo-inverse cutoff is set where FP64 resolves every kept singular vector: there the
+    # gradient is a property of the network, not of the SVD routine.  Two LAPACK drivers (QR
+    # iteration and divide and conquer) must give the same energy and gradient well inside the
+    # 1e-5 parity bar.  (At a cutoff of 1e-8 the same comparison differs by 4e-4.)
+    import scipy.linalg
+    import oracle.ctmrg as oc
+    w = W.custom(2, 2, 2, 6, 3, seeds=[2, 3, 4, 5], terms=W.shastry_sutherland_terms(), name="ss_small")
+    env0 = W.initial_environment(w)
+    out = []
+    orig = oc._svd
+    try:
+        for drv in ("gesvd", "gesdd"):
+            def svd(M, drv=drv):
+                U, s, Vh = scipy.linalg.svd(M.detach().numpy(), full_matrices=True, lapack_driver=drv)
+                return torch.from_numpy(U), torch.from_numpy(s), torch.from_numpy(Vh.T.copy())
+            oc._svd = svd
+            out.append(evaluate(w.tensors, w.Lx, w.Ly, w.chi, w.n_iter, w.terms, env0=env0))
+    finally:
+        oc._svd = orig
+    (E1, g1), (E2, g2) = out
+    g1 = np.concatenate([x.ravel() for x in g1])
+    g2 = np.concatenate([x.ravel() for x in g2])
+    assert abs(E1 - E2) < 1e-12
+    assert np.linalg.norm(g1 - g2) / np.linalg.norm(g1) < 1e-6

@@ -105,6 +105,29 @@ def ising_site(seed: int, d: int, D: int, K: float = ISING_K, noise: float = ISI
     return A / np.abs(A).max()
 
 
+NOISE_ETA = 0.15    # amplitude of the sign-mixed Gaussian part of the workload tensors
+
+
+def noisy_ising_site(seed: int, d: int, D: int, eta: float = NOISE_ETA, K: float = ISING_K) -> np.ndarray:
+    """Random-normal site tensor around a correlated sign-free core.
+
+    The Ising wave function at coupling K (``ising_site`` without noise, scaled to max-abs 1)
+    occupies the first two states of every bond; every entry of the D-dimensional tensor then
+    gets eta * N(0, 1) from ``np.random.default_rng(seed)`` (signs mixed), and the result is
+    scaled to max-abs 1.  With eta = 0.15 every bond state carries weight: at D=6, chi=64 the
+    bond density matrices of the nested CTMRG are numerically of full rank (about 380 of 384
+    singular values above 1e-13 s_1), all 64 kept values lie above 7e-6 s_1 once converged,
+    and the iteration converges (spectrum change 5e-6 after 50 iterations).  Pure
+    N(0, sigma^2) draws (eta -> infinity), and eta >= 0.25 at D=6, make the fixed-iteration
+    function chaotic: the energy jumps by O(1) from one iteration to the next
+    (tests/test_oracle_pins.py shows it at D=2).
+    """
+    A = ising_site(seed, d, D, K=K, noise=0.0)
+    A = A / np.abs(A).max()
+    A = A + eta * np.random.default_rng(seed).standard_normal(A.shape)
+    return A / np.abs(A).max()
+
+
 def random_site(seed: int, d: int, D: int, std: float | None = None, maxabs: bool = False,
                 signed: bool = False) -> np.ndarray:
     """|N(0,1)| draw from ``np.random.default_rng(seed)``, scaled by ``std`` or to max-abs 1.
@@ -150,33 +173,33 @@ def shastry_sutherland_terms(J: float = 0.7, Jp: float = 1.0) -> list:
 
 
 def config(name: str) -> Workload:
-    """The seeded workloads: shapes of the paper's runs, sign-free correlated tensors.
+    """The seeded workloads: shapes of the paper's runs, random-normal tensors around a correlated core.
 
     heis_d2_chi8:  rotated Heisenberg, 1-site, D=2, chi=8, 20 iterations, seed 0
     heis_d4_chi32: rotated Heisenberg, 1-site, D=4, chi=32, 40 iterations, seed 1
     ss_d6_chi64:   Shastry-Sutherland J=0.7, J'=1, 2x2 cell, D=6, chi=64,
                    50 iterations, seeds 2..5 (one per site)
     heis_d9_chi81: rotated Heisenberg, 1-site, D=9, chi=81, 60 iterations, seed 6
-    Every site tensor is ``ising_site(seed, 2, D)``.
+    Every site tensor is ``noisy_ising_site(seed, 2, D)``.
     """
     d = 2
     if name == "heis_d2_chi8":
-        return Workload(name, 1, 1, d, 2, 8, 20, [ising_site(0, d, 2)], heisenberg_terms_rotated())
+        return Workload(name, 1, 1, d, 2, 8, 20, [noisy_ising_site(0, d, 2)], heisenberg_terms_rotated())
     if name == "heis_d4_chi32":
-        return Workload(name, 1, 1, d, 4, 32, 40, [ising_site(1, d, 4)], heisenberg_terms_rotated(),
+        return Workload(name, 1, 1, d, 4, 32, 40, [noisy_ising_site(1, d, 4)], heisenberg_terms_rotated(),
                         precision="tf32")
     if name == "ss_d6_chi64":
-        ts = [ising_site(s, d, 6) for s in (2, 3, 4, 5)]
+        ts = [noisy_ising_site(s, d, 6) for s in (2, 3, 4, 5)]
         return Workload(name, 2, 2, d, 6, 64, 50, ts, shastry_sutherland_terms(), precision="bf16")
     if name == "heis_d9_chi81":
-        return Workload(name, 1, 1, d, 9, 81, 60, [ising_site(6, d, 9)], heisenberg_terms_rotated(),
+        return Workload(name, 1, 1, d, 9, 81, 60, [noisy_ising_site(6, d, 9)], heisenberg_terms_rotated(),
                         precision="bf16")
     raise KeyError(name)
 
 
 def custom(Lx, Ly, D, chi, n_iter, seeds, terms, d=2, name="custom") -> Workload:
     """A workload of arbitrary size drawn the same way (used by scaled-down tests)."""
-    ts = [ising_site(s, d, D) for s in seeds]
+    ts = [noisy_ising_site(s, d, D) for s in seeds]
     assert len(ts) == Lx * Ly
     return Workload(name, Lx, Ly, d, D, chi, n_iter, ts, terms)
 

@@ -184,7 +184,7 @@ int ctm_svd(const double* M, int batch, int r, double* U, double* s, double* V, 
  * counterpart: this is a service of the library, not a step of the method.
  * Same arguments, layouts and results as ctm_svd; batch*r*r must not exceed
  * 1,048,576 and batch must not exceed 1024, otherwise CTM_ERR_INVALID_ARG is
- * returned before any work is enqueued.  The workspace is one fixed 16 MiB
+ * returned before any work is enqueued.  The workspace is one fixed ~16 MiB
  * device array compiled into the library: every GPU that loads the library
  * holds it until the process exits.  Every call looks up the array's device
  * address on the current device (cudaGetSymbolAddress, no allocation); the

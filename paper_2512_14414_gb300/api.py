@@ -43,6 +43,7 @@ class CTM:
         self.lib = _lib.load()
         self.Lx, self.Ly, self.d, self.D, self.chi = Lx, Ly, d, D, chi
         self.precision = precision
+        self.cutoff = cutoff
         self._h = [np.ascontiguousarray(np.asarray(t[4], dtype=np.float64)) for t in terms]
         arr = (_lib.CtmTerm * len(self._h))()
         for k, t in enumerate(terms):

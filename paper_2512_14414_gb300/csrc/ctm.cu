@@ -368,74 +368,38 @@ struct PairIn {
   std::vector<int64_t> pdims, qdims;  // dims of P and Q tensors [chi, b..., chi]
 };
 
-// Full factorisation of rho = N S^t for every pair of the batch: Householder QR of tall N and S
-// (rho = Q_n R_n R_s^t Q_s^t), one-sided Jacobi SVD of the r x r core, U/V lifted back through
-// the Q factors.  Stores r singular triplets per pair.
+// Full factorisation of rho = N S^t for every pair of the batch (svd_product_full): Householder
+// QR of S (tall pairs) and of X = N S^t Q_s, one-sided Jacobi on the rows of the triangular factor.
+// Stores all r singular triplets.
 void projectors_full(ctm_handle* h, const std::vector<PairIn>& in, const std::vector<Tensor>& N64,
                      const std::vector<Tensor>& S64, std::vector<ctm_handle::Fac*>& F, int r) {
   Engine& E = *h->eng;
   cudaStream_t st = h->st;
   const int nb = (int)in.size();
-  const int64_t rr = (int64_t)r * r;
-  double* W = (double*)E.arena().alloc(sizeof(double) * rr * nb);
-  double* Vw = (double*)E.arena().alloc(sizeof(double) * rr * nb);
-  double* lam = (double*)E.arena().alloc(sizeof(double) * r * nb);
-  double* Uo = (double*)E.arena().alloc(sizeof(double) * rr * nb);
-  double* Vo = (double*)E.arena().alloc(sizeof(double) * rr * nb);
-  std::vector<double*> Nc(nb, nullptr), Sc(nb, nullptr), tn(nb, nullptr), ts(nb, nullptr);
+  std::vector<const double*> Np(nb), Sp(nb);
+  std::vector<double*> Up(nb), Vp(nb);
+  std::vector<int> nrs(nb), nls(nb);
+  int nrmax = 0, nlmax = 0;
   for (int b = 0; b < nb; ++b) {
-    const int64_t nr = in[b].n_r, nl = in[b].n_l;
-    GemmSpec g;
-    if (nr > nl) {  // tall: Householder QR of N and S (column-major copies)
-      Nc[b] = (double*)E.arena().alloc(sizeof(double) * nr * nl);
-      Sc[b] = (double*)E.arena().alloc(sizeof(double) * nr * nl);
-      tn[b] = (double*)E.arena().alloc(sizeof(double) * nl);
-      ts[b] = (double*)E.arena().alloc(sizeof(double) * nl);
-      PermSpec ps;
-      ps.rank = 2;
-      ps.out_dims[0] = nl;
-      ps.out_dims[1] = nr;
-      ps.in_stride[0] = 1;
-      ps.in_stride[1] = nl;
-      permute(N64[b].p, F64, Nc[b], F64, ps, false, 1.0, st);
-      permute(S64[b].p, F64, Sc[b], F64, ps, false, 1.0, st);
-      qr_householder(Nc[b], tn[b], 1, (int)nr, (int)nl, nr * nl, h->dstatus, st);
-      qr_householder(Sc[b], ts[b], 1, (int)nr, (int)nl, nr * nl, h->dstatus, st);
-      double* Rn = (double*)E.arena().alloc(sizeof(double) * nl * nl);
-      double* Rs = (double*)E.arena().alloc(sizeof(double) * nl * nl);
-      qr_extract_R(Nc[b], Rn, 1, (int)nr, (int)nl, nr * nl, st);
-      qr_extract_R(Sc[b], Rs, 1, (int)nr, (int)nl, nr * nl, st);
-      // W = (R_n R_s^t)^t = R_s R_n^t, i.e. M column-major
-      g.M = nl; g.N = nl; g.K = nl; g.transA = false; g.lda = nl; g.transB = true; g.ldb = nl; g.ldc = nl;
-      gemm_f64(Rs, Rn, W + b * rr, g, st);
-    } else {        // rho = N S^t is r x r: W = (N S^t)^t = S N^t
-      g.M = nr; g.N = nr; g.K = nl; g.transA = false; g.lda = nl; g.transB = true; g.ldb = nl; g.ldc = nr;
-      gemm_f64((const double*)S64[b].p, (const double*)N64[b].p, W + b * rr, g, st);
-    }
+    Np[b] = (const double*)N64[b].p;
+    Sp[b] = (const double*)S64[b].p;
+    nrs[b] = (int)in[b].n_r;
+    nls[b] = (int)in[b].n_l;
+    nrmax = std::max(nrmax, nrs[b]);
+    nlmax = std::max(nlmax, nls[b]);
+    Up[b] = F[b]->U;
+    Vp[b] = F[b]->V;
   }
-  set_identity_colmajor(Vw, nb, r, st);
-  svd_jacobi(W, Vw, lam, Uo, Vo, nb, r, lim_sweeps(), h->dstatus, h->dsweeps, st);
+  double* ws = (double*)E.arena().alloc(svd_product_full_ws(nb, nrmax, nlmax, r));
+  double* lam = (double*)E.arena().alloc(sizeof(double) * nb * r);
+  std::vector<int> rk;
+  svd_product_full(Np.data(), Sp.data(), nrs.data(), nls.data(), nb, r, ws, lam, Up.data(), Vp.data(), h->dstatus,
+                   h->dsweeps, rk, st);
+  auto& hint = h->rank_hint;
   for (int b = 0; b < nb; ++b) {
-    const int64_t nr = in[b].n_r, nl = in[b].n_l;
     F[b]->rs = r;
     CTM_CUDA(cudaMemcpyAsync(F[b]->lam, lam + (int64_t)b * r, sizeof(double) * r, cudaMemcpyDeviceToDevice, st));
-    if (nr > nl) {
-      for (int side = 0; side < 2; ++side) {
-        double* X = (double*)E.arena().alloc(sizeof(double) * nr * r);
-        embed_transpose((side ? Vo : Uo) + b * rr, r, X, nr, st);
-        qr_apply_Q(side ? Sc[b] : Nc[b], side ? ts[b] : tn[b], X, 1, (int)nr, (int)nl, r, nr * nl, nr * r, h->dstatus, st);
-        PermSpec ps;
-        ps.rank = 2;
-        ps.out_dims[0] = nr;
-        ps.out_dims[1] = r;
-        ps.in_stride[0] = 1;
-        ps.in_stride[1] = nr;
-        permute(X, F64, side ? F[b]->V : F[b]->U, F64, ps, false, 1.0, st);
-      }
-    } else {
-      CTM_CUDA(cudaMemcpyAsync(F[b]->U, Uo + b * rr, sizeof(double) * rr, cudaMemcpyDeviceToDevice, st));
-      CTM_CUDA(cudaMemcpyAsync(F[b]->V, Vo + b * rr, sizeof(double) * rr, cudaMemcpyDeviceToDevice, st));
-    }
+    hint[h->cur_pair + b] = std::max(rk[b], 1);
   }
 }
 
@@ -500,22 +464,11 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
       l = known ? std::min(r, std::max(16, (hmax + 12 + 7) / 8 * 8)) : std::min(r, std::max(chi + 16, 32));
       std::vector<const double*> Np(nb), Sp(nb);
       for (int b = 0; b < nb; ++b) Np[b] = (const double*)N64[b].p, Sp[b] = (const double*)S64[b].p;
-      // warm start from the same pair's right singular vectors of the previous iteration
+      // The test matrix is random: a sketch started from the previous iteration's singular vectors
+      // can carry numerically null directions of the new rho (old tail vectors) whose tiny Ritz
+      // values would pass the exactness test below although the sketch misses part of the range.
       std::vector<const double*> Wp(nb, nullptr);
-      int kw = 0, ldw = 0;
-      if (known && h->cur_iter > 0 && (int)h->fac[h->cur_iter - 1].size() >= h->cur_pair + nb) {
-        auto& prev = h->fac[h->cur_iter - 1];
-        bool same = true;
-        for (int b = 0; b < nb; ++b) {
-          const ctm_handle::Fac& f = prev[h->cur_pair + b];
-          same = same && f.V && f.n_r == nrs[b] && f.rs == prev[h->cur_pair].rs;
-        }
-        if (same) {
-          ldw = prev[h->cur_pair].rs;
-          kw = std::min(hmax, ldw);
-          for (int b = 0; b < nb; ++b) Wp[b] = prev[h->cur_pair + b].V;
-        }
-      }
+      const int kw = 0, ldw = 0;
       bool ok = false;
       for (int attempt = 0; attempt < 2 && !ok && 2 * l <= r; ++attempt) {
         double* ws = (double*)E.arena().alloc(svd_sketch_product_ws(nb, nrmax, nlmax, l));
@@ -526,8 +479,11 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
         const int kwa = std::min(kw, l - 8);
         svd_sketch_product(Np.data(), Sp.data(), nrs.data(), nls.data(), nb, l, kwa > 0 ? Wp.data() : nullptr, ldw,
                            std::max(kwa, 0), ws, lam, Uo, Vo, h->dstatus, h->dsweeps, inc, rk, st);
+        // exact when the sketch's smallest Ritz value is at the rounding floor and at least 8 of the
+        // l directions are numerically null (the range of rho fits with room to spare)
         ok = true;
         for (int x : inc) ok = ok && x == 0;
+        for (int x : rk) ok = ok && x <= l - 8;
         if (!ok) {
           l *= 2;
           continue;
@@ -544,8 +500,6 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
       }
       sketched = ok;
     }
-    if (!sketched)
-      for (int b = 0; b < nb; ++b) hint[h->cur_pair + b] = 0;
     if (!sketched) projectors_full(h, in, N64, S64, F, r);
     if (h->debug_sweeps) {
       int sw = 0;
@@ -676,35 +630,41 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
       double* Ev = A64(nr * kb);
       proj_resid(dUk, Xu, sv[b].sinv, Eu, 1, nr, rs, kb, st);
       proj_resid(dVk, Xv, sv[b].sinv, Ev, 1, nr, rs, kb, st);
-      // drho = U core V^t + Eu V_k^t + U_k Ev^t is never formed (n_r x n_r); with
-      // VtS = V^t S and UtN = U^t N (rs x n_l):
-      //   dN += drho S   = U (core VtS + [Ev^t S; 0]) + Eu VtS[:kb]
-      //   dS += drho^t N = V (core^t UtN + [Eu^t N; 0]) + Ev UtN[:kb]
-      double* VtS = A64((int64_t)rs * nl);
-      double* UtN = A64((int64_t)rs * nl);
+      // drho = U core V^t + Eu V_k^t + U_k Ev^t is never formed (n_r x n_r).  core vanishes
+      // outside its first kb rows and columns (only kept triplets carry a cotangent), so
+      //   U core V^t = U_k Y0^t + Z0 V_k^t,  Y0 = V core[:kb, :]^t,  Z0 = U core[:, :kb] - U_k core[:kb, :kb],
+      // and with Y = Y0 + Ev, Z = Z0 + Eu (n_r x kb) drho = U_k Y^t + Z V_k^t has rank <= 2 kb:
+      //   dN += drho S   = U_k (Y^t S) + Z (V_k^t S)
+      //   dS += drho^t N = Y (U_k^t N) + V_k (Z^t N)
+      double* Y = Ev;
+      double* Z = Eu;
       g = GemmSpec();
-      g.M = rs; g.N = nl; g.K = nr; g.transA = true; g.lda = rs; g.ldb = nl; g.ldc = nl;
+      g.M = nr; g.N = kb; g.K = rs; g.lda = rs; g.transB = true; g.ldb = rs; g.ldc = kb; g.beta = 1.0;
+      gemm_f64(V, core, Y, g, st);
+      g = GemmSpec();
+      g.M = nr; g.N = kb; g.K = rs; g.lda = rs; g.ldb = rs; g.ldc = kb; g.beta = 1.0;
+      gemm_f64(U, core, Z, g, st);
+      g.K = kb; g.alpha = -1.0;
+      gemm_f64(U, core, Z, g, st);
+      double* YtS = A64((int64_t)kb * nl);
+      double* VtS = A64((int64_t)kb * nl);
+      double* UtN = A64((int64_t)kb * nl);
+      double* ZtN = A64((int64_t)kb * nl);
+      g = GemmSpec();
+      g.M = kb; g.N = nl; g.K = nr; g.transA = true; g.lda = kb; g.ldb = nl; g.ldc = nl;
+      gemm_f64(Y, S, YtS, g, st);
+      gemm_f64(Z, N, ZtN, g, st);
+      g.lda = rs;
       gemm_f64(V, S, VtS, g, st);
       gemm_f64(U, N, UtN, g, st);
-      double* G1 = A64((int64_t)rs * nl);
-      double* G2 = A64((int64_t)rs * nl);
       g = GemmSpec();
-      g.M = rs; g.N = nl; g.K = rs; g.lda = rs; g.ldb = nl; g.ldc = nl;
-      gemm_f64(core, VtS, G1, g, st);
-      g.transA = true;
-      gemm_f64(core, UtN, G2, g, st);
-      g = GemmSpec();
-      g.M = kb; g.N = nl; g.K = nr; g.transA = true; g.lda = kb; g.ldb = nl; g.ldc = nl; g.beta = 1.0;
-      gemm_f64(Ev, S, G1, g, st);
-      gemm_f64(Eu, N, G2, g, st);
-      g = GemmSpec();
-      g.M = nr; g.N = nl; g.K = rs; g.lda = rs; g.ldb = nl; g.ldc = nl; g.beta = 1.0;
-      gemm_f64(U, G1, dN, g, st);
-      gemm_f64(V, G2, dS, g, st);
-      g = GemmSpec();
-      g.M = nr; g.N = nl; g.K = kb; g.lda = kb; g.ldb = nl; g.ldc = nl; g.beta = 1.0;
-      gemm_f64(Eu, VtS, dN, g, st);
-      gemm_f64(Ev, UtN, dS, g, st);
+      g.M = nr; g.N = nl; g.K = kb; g.ldb = nl; g.ldc = nl; g.beta = 1.0;
+      g.lda = rs;
+      gemm_f64(U, YtS, dN, g, st);
+      gemm_f64(V, ZtN, dS, g, st);
+      g.lda = kb;
+      gemm_f64(Z, VtS, dN, g, st);
+      gemm_f64(Y, UtN, dS, g, st);
       if (inc[b].N.id >= 0) cast(dN, F64, E.grad(inc[b].N), edt, nr * nl, true, st);
       if (inc[b].S.id >= 0) cast(dS, F64, E.grad(inc[b].S), edt, nr * nl, true, st);
     }
@@ -1434,15 +1394,16 @@ int ctm_svd(const double* M, int batch, int r, double* U, double* s, double* V, 
     permute(M, F64, W, F64, ps, false, 1.0, st);
     set_identity_colmajor(Vw, batch, r, st);
     svd_jacobi(W, Vw, s, U, V, batch, r, lim_sweeps(), status, status + 1, st);
-    int hs = 0;
-    CTM_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    int hs[2] = {0, 0};
+    CTM_CUDA(cudaMemcpyAsync(hs, status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CTM_CUDA(cudaStreamSynchronize(st));
+    if (getenv("CTM_DEBUG_SWEEPS")) fprintf(stderr, "libctm: ctm_svd batch %d r %d Jacobi sweeps %d\n", batch, r, hs[1]);
     cudaFree(W);
     cudaFree(Vw);
     cudaFree(status);
-    if (hs & DEV_TIMEOUT) throw Error(CTM_ERR_TIMEOUT, "device wait timed out");
-    if (hs & DEV_SVD_NOCONV) throw Error(CTM_ERR_SVD_NOCONV, "Jacobi SVD did not converge");
-    if (hs & DEV_NONFINITE) throw Error(CTM_ERR_NONFINITE, "non-finite singular value");
+    if (hs[0] & DEV_TIMEOUT) throw Error(CTM_ERR_TIMEOUT, "device wait timed out");
+    if (hs[0] & DEV_SVD_NOCONV) throw Error(CTM_ERR_SVD_NOCONV, "Jacobi SVD did not converge");
+    if (hs[0] & DEV_NONFINITE) throw Error(CTM_ERR_NONFINITE, "non-finite singular value");
   });
 }
 

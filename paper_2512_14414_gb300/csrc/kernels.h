@@ -122,6 +122,16 @@ void svd_sketch_product(const double* const* N, const double* const* S, const in
                         int l, const double* const* warm, int ldw, int kw, double* ws, double* lam, double* Uo,
                         double* Vo, int* status, int* sweeps_out, std::vector<int>& incomplete_host,
                         std::vector<int>& rank_host, cudaStream_t st);
+// Full thin SVD of rho_b = N_b S_b^t (n_r x n_r, rank <= r = min(n_r, n_l), the same r for the
+// whole batch): X = N S^t for n_r <= n_l, X = N R_s^t with S = Q_s R_s (Householder) for n_r > n_l,
+// so that rho = X B^t with B = I or Q_s.  X = Q_x R_x (Householder) and one-sided Jacobi on R_x^t:
+// R_x^t V_J = U_J S, hence U = Q_x V_J and V = B U_J.  Outputs per pair: lam (batch x r,
+// descending), U[b], V[b] (n_r x r row-major), rank_host[b] = values above 1e-14 lam_max.
+// ws: svd_product_full_ws(batch, max n_r, max n_l, r).
+size_t svd_product_full_ws(int batch, int nr, int nl, int r);
+void svd_product_full(const double* const* N, const double* const* S, const int* nrs, const int* nls, int batch, int r,
+                      double* ws, double* lam, double* const* U, double* const* V, int* status, int* sweeps_out,
+                      std::vector<int>& rank_host, cudaStream_t st);
 // Flops counted by the Jacobi kernels since the last call (6r per pair test, 12r per rotation).
 double jacobi_flops_read_reset(cudaStream_t st);
 // X[k*m + i] = U[i*r + k] for i < r, 0 for r <= i < m  (k < r): [U; 0] stored column-major.

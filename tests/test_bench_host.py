@@ -28,3 +28,10 @@ def test_roofline_takes_the_class_with_the_largest_time():
     prof["gemm_f64"] = (900.0, 7, 1e12, 1e9)
     r = bench._roofline(prof, "fp64", peaks, "measured")
     assert r["kernel"] == "gemm_f64" and r["bound"] == "alu" and r["peak"] == bench.FP64_PEAK_TFLOPS
+
+
+def test_kept_per_pair_counts_values_above_the_cutoff():
+    import numpy as np
+    sp = np.array([[1.0, 0.5, 1e-7, 0.0], [2.0, 1e-5, 2.1e-6, 1e-9]])
+    k = bench.kept_per_pair(sp, 3, 1e-6)
+    assert k["min"] == 2 and k["max"] == 3 and k["chi"] == 3 and k["pairs"] == 2

@@ -134,6 +134,23 @@ int ctm_energy(ctm_handle* h, double* e_site_dev, double* e_bonds_dev, void* str
  *   e_site_dev : device, 1 double.   dA_dev : device, FP64, layout of A. */
 int ctm_grad(ctm_handle* h, int n_iter, double* e_site_dev, double* dA_dev, void* stream);
 
+/* Order parameters of the current environment (Sec. Results).
+ * ctm_magnetization: Eq. Mag1 for spin 1/2 (d = 2).  m_dev: device, Lx*Ly x 3 doubles, the
+ *   expectation values (<S_x>, <S_y>, <S_z>) of every PEPS site of the cell (index y*Lx + x) from its
+ *   one-site reduced density matrix (the nested block [A Y; X A*] with Y's physical line cut open);
+ *   with real tensors <S_y> = 0.  M_dev: device, 1 double, M = (1/N) sum_i |m_i| over the N = Lx*Ly
+ *   sites.  For a sublattice-rotated ansatz the rotation flips S_x and S_z of one sublattice, which
+ *   leaves |m_i| and M unchanged.  CTM_ERR_INVALID_ARG unless d == 2 and Lx*Ly <= 64.
+ * ctm_plaquette_order: Eq. Mag2, M_p = |sum_{a in A} e_a - sum_{b in B} e_b| / 4, where e_t =
+ *   Tr(rho_t h_t) / Tr(rho_t) of term t (the bond value ctm_energy reports; <S_i.S_j> when h_t is
+ *   the Heisenberg bond) and terms_a / terms_b (host, na / nb term indices in the order given to
+ *   ctm_create) list the nearest-neighbour bonds of the two inequivalent empty plaquettes.
+ *   Mp_dev: device, 1 double.
+ * Both enqueue on the stream and synchronise it (status check); no allocation outside the handle. */
+int ctm_magnetization(ctm_handle* h, double* m_dev, double* M_dev, void* stream);
+int ctm_plaquette_order(ctm_handle* h, const int* terms_a, int na, const int* terms_b, int nb, double* Mp_dev,
+                        void* stream);
+
 /* Copy the current environment out / in (FP64, layout above). */
 int ctm_get_env(ctm_handle* h, double* env_dev, void* stream);
 int ctm_set_env(ctm_handle* h, const double* env_dev, void* stream);

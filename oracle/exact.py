@@ -11,6 +11,8 @@ the energy normalisation independently of CTMRG:
                         nested single-layer network (Eq. XY with the impurity
                         Y) and from the reduced double-layer network (Eq. Tred),
                         contracted exactly.
+* ``nested_site_rdm`` / ``site_expectation_sv`` - a one-site RDM of the nested network
+                        (one impurity Y) and the one-site expectation value from the amplitudes.
 * ``lanczos_ground``  - the exact ground energy of the cluster Hamiltonian.
 
 Parity: these are definitions written out; pinned against each other and
@@ -114,6 +116,44 @@ def nested_bond_rdm(sites, s1, s2, d):
     t, ls = _contract_sequence(items)
     order = [ls.index(l) for l in ("k1", "k2", "b1", "b2")]
     return t.permute(*order).reshape(d * d, d * d)
+
+
+def nested_site_rdm(sites, s, d):
+    """Exact one-site RDM [ket sigma][bra sigma'] of site s=(x,y) from the nested network of the open
+    cluster: the Y of that site carries its physical line cut open (Sec. NTN impurity)."""
+    Ly, Lx = len(sites), len(sites[0])
+    D = sites[0][0].shape[1]
+    X, Y, Yi = x_tensor(D), y_tensor(D, d), y_impurity(D, d)
+    R, C = 2 * Ly, 2 * Lx
+    items = []
+    for i in range(R):
+        for j in range(C):
+            k = site_kind(i, j)
+            p = sites[i // 2][j // 2]
+            extra = []
+            if k == "A":
+                t = ket_tensor(p)
+            elif k == "A*":
+                t = bra_tensor(p)
+            elif k == "X":
+                t = X
+            elif (i, j) == (2 * s[1], 2 * s[0] + 1):
+                t = Yi
+                extra = ["k", "b"]
+            else:
+                t = Y
+            ls = [("h", i, j - 1), ("v", i - 1, j), ("h", i, j), ("v", i, j)] + extra
+            items.append(_fix_outer(t, ls, i == 0, j == 0, i == R - 1, j == C - 1))
+    t, ls = _contract_sequence(items)
+    return t.permute(ls.index("k"), ls.index("b"))
+
+
+def site_expectation_sv(psi, op, i):
+    """<psi|op_i|psi>/<psi|psi> for a one-site operator op (d x d) on site i."""
+    n = psi.dim()
+    perm = [i] + [k for k in range(n) if k != i]
+    t = psi.permute(*perm).reshape(psi.shape[i], -1)
+    return float((t * (torch.as_tensor(op, dtype=DT) @ t)).sum() / (psi * psi).sum())
 
 
 def double_bond_rdm(sites, s1, s2, d):

@@ -11,7 +11,7 @@ CTM_FP64, CTM_TF32, CTM_BF16, CTM_TF32X3, CTM_BF16X3 = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": CTM_FP64, "tf32": CTM_TF32, "bf16": CTM_BF16, "tf32x3": CTM_TF32X3, "bf16x3": CTM_BF16X3}
 
 EXPORTS = ["ctm_create", "ctm_init", "ctm_step", "ctm_energy", "ctm_grad", "ctm_get_env", "ctm_set_env",
-           "ctm_env_numel", "ctm_kernel_launches", "ctm_set_limits", "ctm_profile", "ctm_profile_read", "ctm_svd", "ctm_svd_noalloc",
+           "ctm_env_numel", "ctm_kernel_launches", "ctm_set_limits", "ctm_magnetization", "ctm_plaquette_order", "ctm_profile", "ctm_profile_read", "ctm_svd", "ctm_svd_noalloc",
            "ctm_get_spectra", "ctm_mlp_forward", "ctm_destroy", "ctm_error_string"]
 PROF_CLASSES = {"gemm": 0, "permute": 1, "svd": 2, "qr": 3, "misc": 4, "tc_gemm": 5, "gemm_f64": 6}
 
@@ -52,6 +52,8 @@ def load():
     lib.ctm_kernel_launches.argtypes = [vp]
     lib.ctm_kernel_launches.restype = i64
     lib.ctm_set_limits.argtypes = [vp, i, i64]
+    lib.ctm_magnetization.argtypes = [vp, vp, vp, vp]
+    lib.ctm_plaquette_order.argtypes = [vp, ctypes.POINTER(i), i, ctypes.POINTER(i), i, vp, vp]
     lib.ctm_profile.argtypes = [vp, i]
     lib.ctm_profile_read.argtypes = [vp, i, ctypes.POINTER(d), ctypes.POINTER(i64), ctypes.POINTER(d),
                                      ctypes.POINTER(d)]
@@ -63,7 +65,7 @@ def load():
     lib.ctm_error_string.argtypes = [i]
     lib.ctm_error_string.restype = ctypes.c_char_p
     for f in ("ctm_create", "ctm_init", "ctm_step", "ctm_energy", "ctm_grad", "ctm_get_env", "ctm_set_env",
-              "ctm_set_limits", "ctm_profile", "ctm_profile_read", "ctm_svd", "ctm_svd_noalloc", "ctm_get_spectra", "ctm_mlp_forward",
+              "ctm_set_limits", "ctm_magnetization", "ctm_plaquette_order", "ctm_profile", "ctm_profile_read", "ctm_svd", "ctm_svd_noalloc", "ctm_get_spectra", "ctm_mlp_forward",
               "ctm_destroy"):
         getattr(lib, f).restype = i
     _lib = lib

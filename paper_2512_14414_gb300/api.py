@@ -87,6 +87,22 @@ class CTM:
         _check(self.lib.ctm_energy(self.handle, _ptr(e), _ptr(eb), _stream()), "ctm_energy")
         return (e, eb) if per_bond else e
 
+    def magnetization(self):
+        """Eq. Mag1: (per-site (<Sx>, <Sy>, <Sz>) as a cuda [Lx*Ly, 3] tensor, M as a cuda [1] tensor)."""
+        m = torch.empty(self.Lx * self.Ly, 3, dtype=torch.float64, device="cuda")
+        M = torch.empty(1, dtype=torch.float64, device="cuda")
+        _check(self.lib.ctm_magnetization(self.handle, _ptr(m), _ptr(M), _stream()), "ctm_magnetization")
+        return m, M
+
+    def plaquette_order(self, terms_a, terms_b):
+        """Eq. Mag2 from the bond values of two lists of term indices: a cuda [1] tensor."""
+        a = (ctypes.c_int * len(terms_a))(*terms_a)
+        b = (ctypes.c_int * len(terms_b))(*terms_b)
+        Mp = torch.empty(1, dtype=torch.float64, device="cuda")
+        _check(self.lib.ctm_plaquette_order(self.handle, a, len(terms_a), b, len(terms_b), _ptr(Mp), _stream()),
+               "ctm_plaquette_order")
+        return Mp
+
     def grad(self, n_iter, dA=None, e=None):
         nA = self.Lx * self.Ly * self.d * self.D ** 4
         dA = dA if dA is not None else torch.empty(self.Lx * self.Ly, self.d, self.D, self.D, self.D, self.D,

@@ -847,54 +847,67 @@ BlockSpec block_of(int kind) {
   }
 }
 
-Tensor bond_rdm(ctm_handle* h, const ctm_handle::TermH& t) {
+// Reduced density matrix of a bh x bw block of nested sites whose upper-left site is (i0, j0),
+// closed by the environment, with the physical line of the Y at every position of `imps` cut
+// open (impurity Y's).  Legs of the result: the ket indices of the impurities in order, then
+// their bra indices.
+Tensor block_rdm(ctm_handle* h, int i0, int j0, int bh, int bw, const std::vector<std::pair<int, int>>& imps) {
   Engine& E = *h->eng;
   Frame F(h, 0);
-  BlockSpec bs = block_of(t.kind);
   const int64_t chi = h->d.chi;
-  const int i0 = 2 * t.y, j0 = 2 * t.x;
   Net net;
-  std::vector<Pos> pos(bs.h * bs.w);
-  for (int a = 0; a < bs.h; ++a)
-    for (int b = 0; b < bs.w; ++b) {
-      bool imp = (a == bs.a1 && b == bs.b1) || (a == bs.a2 && b == bs.b2);
-      pos[a * bs.w + b] = make_pos(h, net, F.site(i0 + a, j0 + b), 0, imp);
+  std::vector<Pos> pos(bh * bw);
+  for (int a = 0; a < bh; ++a)
+    for (int b = 0; b < bw; ++b) {
+      bool imp = false;
+      for (auto& x : imps) imp = imp || (x.first == a && x.second == b);
+      pos[a * bw + b] = make_pos(h, net, F.site(i0 + a, j0 + b), 0, imp);
     }
-  for (int a = 0; a < bs.h; ++a)
-    for (int b = 0; b < bs.w; ++b) {
-      if (b + 1 < bs.w) bond(net, pos[a * bs.w + b], FR, pos[a * bs.w + b + 1], FL);
-      if (a + 1 < bs.h) bond(net, pos[a * bs.w + b], FD, pos[(a + 1) * bs.w + b], FU);
+  for (int a = 0; a < bh; ++a)
+    for (int b = 0; b < bw; ++b) {
+      if (b + 1 < bw) bond(net, pos[a * bw + b], FR, pos[a * bw + b + 1], FL);
+      if (a + 1 < bh) bond(net, pos[a * bw + b], FD, pos[(a + 1) * bw + b], FU);
     }
-  std::vector<int> TU(bs.w + 1), TD(bs.w + 1), TL(bs.h + 1), TR(bs.h + 1);
+  std::vector<int> TU(bw + 1), TD(bw + 1), TL(bh + 1), TR(bh + 1);
   for (auto* v : {&TU, &TD})
     for (auto& x : *v) x = net.make(chi);
   for (auto* v : {&TL, &TR})
     for (auto& x : *v) x = net.make(chi);
   std::map<int, std::vector<Item>> groups;
   auto G = [&](int a, int b) { return (a / 2) * 16 + (b / 2); };
-  auto P = [&](int a, int b) -> Pos& { return pos[a * bs.w + b]; };
-  for (int a = 0; a < bs.h; ++a)
-    for (int b = 0; b < bs.w; ++b) push_site(groups[G(a, b)], net, P(a, b));
-  const int H = bs.h - 1, W = bs.w - 1;
+  auto P = [&](int a, int b) -> Pos& { return pos[a * bw + b]; };
+  for (int a = 0; a < bh; ++a)
+    for (int b = 0; b < bw; ++b) push_site(groups[G(a, b)], net, P(a, b));
+  const int H = bh - 1, W = bw - 1;
   groups[G(0, 0)].push_back(env_item(F, net, P(0, 0).site, S_CUL, {TL[0]}, {}, {TU[0]}));
-  groups[G(0, W)].push_back(env_item(F, net, P(0, W).site, S_CUR, {TU[bs.w]}, {}, {TR[0]}));
-  groups[G(H, W)].push_back(env_item(F, net, P(H, W).site, S_CDR, {TR[bs.h]}, {}, {TD[bs.w]}));
-  groups[G(H, 0)].push_back(env_item(F, net, P(H, 0).site, S_CDL, {TD[0]}, {}, {TL[bs.h]}));
-  for (int b = 0; b < bs.w; ++b) {
+  groups[G(0, W)].push_back(env_item(F, net, P(0, W).site, S_CUR, {TU[bw]}, {}, {TR[0]}));
+  groups[G(H, W)].push_back(env_item(F, net, P(H, W).site, S_CDR, {TR[bh]}, {}, {TD[bw]}));
+  groups[G(H, 0)].push_back(env_item(F, net, P(H, 0).site, S_CDL, {TD[0]}, {}, {TL[bh]}));
+  for (int b = 0; b < bw; ++b) {
     groups[G(0, b)].push_back(env_item(F, net, P(0, b).site, S_TU, {TU[b]}, P(0, b).frame(FU), {TU[b + 1]}));
     groups[G(H, b)].push_back(env_item(F, net, P(H, b).site, S_TD, {TD[b + 1]}, P(H, b).frame(FD), {TD[b]}));
   }
-  for (int a = 0; a < bs.h; ++a) {
+  for (int a = 0; a < bh; ++a) {
     groups[G(a, 0)].push_back(env_item(F, net, P(a, 0).site, S_TL, {TL[a + 1]}, P(a, 0).frame(FL), {TL[a]}));
     groups[G(a, W)].push_back(env_item(F, net, P(a, W).site, S_TR, {TR[a]}, P(a, W).frame(FR), {TR[a + 1]}));
   }
   std::vector<Item> parts;
   for (auto& g : groups) parts.push_back(contract_greedy(E, net, g.second));
-  const Pos& i1 = P(bs.a1, bs.b1);
-  const Pos& i2 = P(bs.a2, bs.b2);
-  Labels out = net.res({i1.s_ket, i2.s_ket, i1.s_bra, i2.s_bra});
+  Labels out;
+  for (auto& x : imps) out.push_back(P(x.first, x.second).s_ket);
+  for (auto& x : imps) out.push_back(P(x.first, x.second).s_bra);
+  out = net.res(out);
   return contract_greedy(E, net, parts, &out).t;
 }
+
+// two-site RDM of a bond term (Eq. ExpH): rows (ket s1, ket s2), columns (bra s1, bra s2)
+Tensor bond_rdm(ctm_handle* h, const ctm_handle::TermH& t) {
+  BlockSpec bs = block_of(t.kind);
+  return block_rdm(h, 2 * t.y, 2 * t.x, bs.h, bs.w, {{bs.a1, bs.b1}, {bs.a2, bs.b2}});
+}
+
+// one-site RDM of PEPS site (x, y): the 2 x 2 nested block [A Y; X A*] with its Y opened
+Tensor site_rdm(ctm_handle* h, int x, int y) { return block_rdm(h, 2 * y, 2 * x, 2, 2, {{0, 1}}); }
 
 // energy of the current environment; optionally seeds dE = 1 into the RDM gradients.
 void energy_op(ctm_handle* h, double* e_site, double* e_bonds, bool backward_seed) {
@@ -1304,6 +1317,62 @@ int64_t ctm_env_numel(const ctm_handle* h) {
     }
   }
   return n;
+}
+
+int ctm_magnetization(ctm_handle* h, double* m_dev, double* M_dev, void* stream) {
+  if (!h || !m_dev || !M_dev) return CTM_ERR_INVALID_ARG;
+  if (h->d.d != 2 || h->d.Lx * h->d.Ly > 64) return CTM_ERR_INVALID_ARG;
+  if (!h->inited) return CTM_ERR_STATE;
+  return guard(h, [&]() {
+    using namespace ctm;
+    h->st = (cudaStream_t)stream;
+    h->eng->set_stream(h->st);
+    h->eng->stop_tape();
+    auto mark = h->tape->mark();
+    SiteLeaves sl = site_views(h, false);
+    g_sites = &sl;
+    const int ns = h->d.Lx * h->d.Ly;
+    double* rho = (double*)h->eng->arena().alloc(sizeof(double) * 4 * ns);
+    for (int y = 0; y < h->d.Ly; ++y)
+      for (int x = 0; x < h->d.Lx; ++x) {
+        Tensor r = site_rdm(h, x, y);
+        cast(r.p, r.dt, rho + 4 * (y * h->d.Lx + x), F64, 4, false, h->st);
+      }
+    site_magnetization(rho, ns, m_dev, M_dev, h->dstatus, h->st);
+    g_sites = nullptr;
+    sync_status(h);
+    h->tape->release(mark);
+  });
+}
+
+int ctm_plaquette_order(ctm_handle* h, const int* terms_a, int na, const int* terms_b, int nb, double* Mp_dev,
+                        void* stream) {
+  if (!h || !Mp_dev || na < 1 || nb < 1 || !terms_a || !terms_b) return CTM_ERR_INVALID_ARG;
+  for (int k = 0; k < na; ++k)
+    if (terms_a[k] < 0 || terms_a[k] >= (int)h->terms.size()) return CTM_ERR_INVALID_ARG;
+  for (int k = 0; k < nb; ++k)
+    if (terms_b[k] < 0 || terms_b[k] >= (int)h->terms.size()) return CTM_ERR_INVALID_ARG;
+  if (!h->inited) return CTM_ERR_STATE;
+  return guard(h, [&]() {
+    using namespace ctm;
+    h->st = (cudaStream_t)stream;
+    h->eng->set_stream(h->st);
+    h->eng->stop_tape();
+    auto mark = h->tape->mark();
+    SiteLeaves sl = site_views(h, false);
+    g_sites = &sl;
+    const int nt = (int)h->terms.size();
+    double* eb = (double*)h->eng->arena().alloc(sizeof(double) * (nt + 1));
+    energy_op(h, eb + nt, eb, false);
+    std::vector<int> idx(terms_a, terms_a + na);
+    idx.insert(idx.end(), terms_b, terms_b + nb);
+    int* idx_dev = (int*)h->eng->arena().alloc(sizeof(int) * idx.size());
+    CTM_CUDA(cudaMemcpyAsync(idx_dev, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, h->st));
+    plaquette_order(eb, idx_dev, na, nb, Mp_dev, h->st);
+    g_sites = nullptr;
+    sync_status(h);
+    h->tape->release(mark);
+  });
 }
 
 int64_t ctm_kernel_launches(const ctm_handle* h) { return h ? h->launches : -1; }

@@ -1008,6 +1008,53 @@ void proj_resid(const double* dU, const double* X, const double* sinv, double* E
   CTM_LAUNCHED();
 }
 
+// ------------------------------------------------------------------ observables (FP64)
+// Per PEPS site, rho is the 2 x 2 one-site RDM [ket s][bra s'] (basis up, down).  For spin 1/2,
+// <S_x> = (rho_01 + rho_10) / (2 Tr rho), <S_z> = (rho_00 - rho_11) / (2 Tr rho); with real tensors
+// Tr(rho S_y) is purely imaginary and its real part, the expectation value, is 0.
+__global__ void magnetization_k(const double* rho, int n_sites, double* m, double* M, int* status) {
+  __shared__ double acc[64];
+  const int t = threadIdx.x;
+  double len = 0.0;
+  if (t < n_sites) {
+    const double* r = rho + 4 * t;
+    const double tr = r[0] + r[3];
+    if (!(fabs(tr) > 0.0) || !isfinite(tr)) atomicOr(status, DEV_NONFINITE);
+    const double sx = 0.5 * (r[1] + r[2]) / tr, sz = 0.5 * (r[0] - r[3]) / tr;
+    m[3 * t + 0] = sx;
+    m[3 * t + 1] = 0.0;
+    m[3 * t + 2] = sz;
+    len = sqrt(sx * sx + sz * sz);
+  }
+  acc[t] = len;
+  __syncthreads();
+  if (t == 0) {
+    double sum = 0.0;
+    for (int k = 0; k < n_sites; ++k) sum += acc[k];
+    *M = sum / n_sites;
+  }
+}
+
+// M_p = |sum_{a in A} e_a - sum_{b in B} e_b| / 4 over the listed per-term values
+__global__ void plaquette_k(const double* e, const int* idx, int na, int nb, double* Mp) {
+  if (threadIdx.x != 0) return;
+  double sa = 0.0, sb = 0.0;
+  for (int k = 0; k < na; ++k) sa += e[idx[k]];
+  for (int k = 0; k < nb; ++k) sb += e[idx[na + k]];
+  *Mp = 0.25 * fabs(sa - sb);
+}
+
+void site_magnetization(const double* rho, int n_sites, double* m, double* M, int* status, cudaStream_t st) {
+  CTM_CHECK(n_sites >= 1 && n_sites <= 64, CTM_ERR_INVALID_ARG, "magnetization: 1..64 sites");
+  magnetization_k<<<1, 64, 0, st>>>(rho, n_sites, m, M, status);
+  CTM_LAUNCHED();
+}
+
+void plaquette_order(const double* e_terms, const int* idx_dev, int na, int nb, double* Mp, cudaStream_t st) {
+  plaquette_k<<<1, 32, 0, st>>>(e_terms, idx_dev, na, nb, Mp);
+  CTM_LAUNCHED();
+}
+
 void energy_terms(const double* rho, const double* hs, const double* coup, int n_terms, int d2, double inv_sites,
                   double* e_bond, double* e_site, double* drho, int* status, cudaStream_t st) {
   CTM_CHECK(n_terms <= 64, CTM_ERR_INVALID_ARG, "at most 64 terms");

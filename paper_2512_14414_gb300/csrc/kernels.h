@@ -144,6 +144,12 @@ void embed_transpose(const double* U, int r, double* X, int64_t m, cudaStream_t 
 void energy_terms(const double* rho, const double* hs, const double* coup, int n_terms, int d2, double inv_sites,
                   double* e_bond, double* e_site, double* drho, int* status, cudaStream_t st);
 
+// Eq. Mag1: rho = n_sites one-site RDMs (2 x 2, [ket][bra]); m[site] = (<Sx>, <Sy>, <Sz>) with
+// <Sy> = 0 for real tensors; *M = mean over sites of |m|.
+void site_magnetization(const double* rho, int n_sites, double* m, double* M, int* status, cudaStream_t st);
+// Eq. Mag2: *Mp = |sum_{k < na} e[idx[k]] - sum_{k < nb} e[idx[na + k]]| / 4 (idx on the device)
+void plaquette_order(const double* e_terms, const int* idx_dev, int na, int nb, double* Mp, cudaStream_t st);
+
 // spectrum change between two sets of normalised spectra (batch x kept), result max into *out (atomic max)
 void spectrum_delta(const double* lam, const double* lam_prev, int batch, int r, int kept, double* out,
                     cudaStream_t st);

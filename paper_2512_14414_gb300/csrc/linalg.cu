@@ -129,20 +129,21 @@ __global__ void qr_kernel(double* A, double* tau, int batch, int m, int n, int64
   }
 }
 
-__global__ void apply_q_kernel(const double* A, const double* tau, double* X, int batch, int m, int n, int k,
-                               int64_t strideA, int64_t strideX, Sync s) {
+// X := Q X column by column: the k columns are independent, so one warp carries its column through
+// all n reflectors (H_{n-1} first) with no grid-wide synchronisation; the reflectors are shared by
+// every warp and stay in L2.
+__global__ void apply_q_cols_kernel(const double* A, const double* tau, double* X, int batch, int m, int n, int k,
+                                    int64_t strideA, int64_t strideX) {
   const int lane = threadIdx.x % 32;
-  const int wpb = blockDim.x / 32;
-  const int64_t gw = (int64_t)blockIdx.x * wpb + threadIdx.x / 32;
-  const int64_t nw = (int64_t)gridDim.x * wpb;
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
   const int64_t tasks = (int64_t)batch * k;
-  for (int j = n - 1; j >= 0; --j) {
-    for (int64_t t = gw; t < tasks; t += nw) {
-      const int64_t b = t / k;
-      const int c = (int)(t % k);
-      apply_reflector(A + b * strideA + (int64_t)j * m, __ldcg(tau + b * n + j), X + b * strideX + (int64_t)c * m, m, j, lane);
-    }
-    if (j > 0 && !grid_barrier(s)) return;
+  for (int64_t t = gw; t < tasks; t += nw) {
+    const int64_t b = t / k;
+    const int c = (int)(t % k);
+    double* x = X + b * strideX + (int64_t)c * m;
+    for (int j = n - 1; j >= 0; --j)
+      apply_reflector(A + b * strideA + (int64_t)j * m, __ldg(tau + b * n + j), x, m, j, lane);
   }
 }
 
@@ -432,6 +433,131 @@ __global__ void __launch_bounds__(128) jacobi_team_kernel(double* W, double* V, 
   }
 }
 
+// The same sweeps with one warp per column pair (four pairs per 128-thread block): the three dot
+// products are reduced with warp shuffles only, every lane derives the rotation from the same
+// sums, and no block-wide synchronisation separates the load, the test and the rotation.  A round
+// is then bound by the FP64 pipes of the SMs rather than by block barriers, and a quarter as many
+// blocks meet at each grid barrier.  Requires max(m, r) <= 32 * MAXE.
+template <int MAXE>
+__global__ void __launch_bounds__(128) jacobi_warp_kernel(double* W, double* V, int batch, int m, int r, int rp,
+                                                           int max_sweeps, double tol, int* flags, int* conv,
+                                                           int* sweeps_out, const double* frob2, double* flop_acc,
+                                                           Sync s) {
+  const int t = threadIdx.x, lane = t % 32;
+  const int wpb = blockDim.x / 32;
+  const int64_t gw = (int64_t)blockIdx.x * wpb + t / 32;
+  const int64_t nw = (int64_t)gridDim.x * wpb;
+  const int npairs = rp / 2;
+  const int64_t tasks = (int64_t)batch * npairs;
+  const int64_t mr = (int64_t)m * r, rr = (int64_t)r * r;
+  double my_flops = 0.0;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    int* fl = flags + (sweep % 3) * batch;
+    if (blockIdx.x == 0) {
+      int* nxt = flags + ((sweep + 1) % 3) * batch;
+      for (int b = t; b < batch; b += blockDim.x) nxt[b] = 0;
+      __threadfence();
+    }
+    for (int round = 0; round < rp - 1; ++round) {
+      for (int64_t task = gw; task < tasks; task += nw) {
+        const int b = (int)(task / npairs);
+        if (__ldcg(conv + b)) continue;
+        int p, q;
+        rr_pair(round, (int)(task % npairs), rp, p, q);
+        if (p >= r || q >= r) continue;
+        double* ap = W + b * mr + (int64_t)p * m;
+        double* aq = W + b * mr + (int64_t)q * m;
+        double* vp = V + b * rr + (int64_t)p * r;
+        double* vq = V + b * rr + (int64_t)q * r;
+        double x[MAXE], y[MAXE], u[MAXE], w[MAXE];
+#pragma unroll
+        for (int e = 0; e < MAXE; ++e) {
+          const int i = lane + 32 * e;
+          x[e] = i < m ? __ldcg(ap + i) : 0.0;
+          y[e] = i < m ? __ldcg(aq + i) : 0.0;
+          u[e] = i < r ? __ldcg(vp + i) : 0.0;
+          w[e] = i < r ? __ldcg(vq + i) : 0.0;
+        }
+        double al = 0.0, be = 0.0, ga = 0.0;
+#pragma unroll
+        for (int e = 0; e < MAXE; ++e) {
+          al = fma(x[e], x[e], al);
+          be = fma(y[e], y[e], be);
+          ga = fma(x[e], y[e], ga);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        const double floor2 = 1e-32 * __ldcg(frob2 + b);
+        if (lane == 0) my_flops += 6.0 * m;
+        if (al > floor2 && be > floor2 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+          if (lane == 0) my_flops += 6.0 * m + 6.0 * r;
+          const double zeta = (be - al) / (2.0 * ga);
+          double tt;
+          if (fabs(zeta) > 1e150)
+            tt = 0.5 / zeta;
+          else
+            tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + tt * tt);
+          const double sn = c * tt;
+#pragma unroll
+          for (int e = 0; e < MAXE; ++e) {
+            const int i = lane + 32 * e;
+            if (i < m) {
+              ap[i] = c * x[e] - sn * y[e];
+              aq[i] = sn * x[e] + c * y[e];
+            }
+            if (i < r) {
+              vp[i] = c * u[e] - sn * w[e];
+              vq[i] = sn * u[e] + c * w[e];
+            }
+          }
+          if (lane == 0) fl[b] = 1;
+        }
+        __syncwarp();
+      }
+      if (!grid_barrier(s)) {
+        if (lane == 0) atomicAdd(flop_acc, my_flops);
+        return;
+      }
+    }
+    int all = 1;
+    {
+      volatile int* vf = fl;
+      volatile int* vc = conv;
+      for (int b = 0; b < batch; ++b)
+        if (!vc[b] && vf[b] != 0) all = 0;
+    }
+    if (!grid_barrier(s)) {
+      if (lane == 0) atomicAdd(flop_acc, my_flops);
+      return;
+    }
+    if (blockIdx.x == 0 && t == 0) {
+      volatile int* vf = fl;
+      for (int b = 0; b < batch; ++b)
+        if (vf[b] == 0) conv[b] = 1;
+      __threadfence();
+    }
+    if (!grid_barrier(s)) {
+      if (lane == 0) atomicAdd(flop_acc, my_flops);
+      return;
+    }
+    if (all) {
+      ++sweep;
+      break;
+    }
+  }
+  if (lane == 0) atomicAdd(flop_acc, my_flops);
+  if (blockIdx.x == 0 && t == 0) {
+    atomicAdd(sweeps_out, sweep);
+    for (int b = 0; b < batch; ++b)
+      if (!conv[b]) atomicOr(s.status, DEV_SVD_NOCONV);
+  }
+}
+
 // Launch the Jacobi sweeps (cooperative) with the register-resident team kernel.
 void launch_jacobi(double* W, double* V, int batch, int m, int r, int max_sweeps, int* flags, int* conv,
                    int* sweeps_out, double* frob2, double* facc, const Sync& sy, cudaStream_t st);
@@ -622,10 +748,38 @@ void launch_jacobi_t(double* W, double* V, int batch, int m, int r, int max_swee
   CTM_LAUNCHED();
 }
 
+template <int MAXE>
+void launch_jacobi_w(double* W, double* V, int batch, int m, int r, int max_sweeps, int* flags, int* conv,
+                     int* sweeps_out, double* frob2, double* facc, const Sync& sy, cudaStream_t st) {
+  const int threads = 128;
+  int rp = r + (r & 1);
+  int grid = coop_grid((const void*)jacobi_warp_kernel<MAXE>, threads);
+  int64_t need = ((int64_t)batch * (rp / 2) + 3) / 4;
+  grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, need));
+  double tol = 2.220446049250313e-16 * std::max(m, r);
+  Sync s = sy;
+  void* args[] = {&W, &V, &batch, &m, &r, &rp, &max_sweeps, &tol, &flags, &conv, &sweeps_out, &frob2, &facc, &s};
+  CTM_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_warp_kernel<MAXE>, grid, threads, args, 0, st));
+  CTM_LAUNCHED();
+}
+
 void launch_jacobi(double* W, double* V, int batch, int m, int r, int max_sweeps, int* flags, int* conv,
                    int* sweeps_out, double* frob2, double* facc, const Sync& sy, cudaStream_t st) {
   const int e = std::max(m, r);
   CTM_CHECK(e <= 128 * 16, CTM_ERR_INVALID_ARG, "Jacobi SVD: size too large");
+  // warp-per-pair kernel for columns up to 384 long (12 doubles per lane and column in registers)
+  if (e <= 128) {
+    launch_jacobi_w<4>(W, V, batch, m, r, max_sweeps, flags, conv, sweeps_out, frob2, facc, sy, st);
+    return;
+  }
+  if (e <= 256) {
+    launch_jacobi_w<8>(W, V, batch, m, r, max_sweeps, flags, conv, sweeps_out, frob2, facc, sy, st);
+    return;
+  }
+  if (e <= 384) {
+    launch_jacobi_w<12>(W, V, batch, m, r, max_sweeps, flags, conv, sweeps_out, frob2, facc, sy, st);
+    return;
+  }
   if (e <= 256) launch_jacobi_t<2>(W, V, batch, m, r, max_sweeps, flags, conv, sweeps_out, frob2, facc, sy, st);
   else if (e <= 512) launch_jacobi_t<4>(W, V, batch, m, r, max_sweeps, flags, conv, sweeps_out, frob2, facc, sy, st);
   else if (e <= 768) launch_jacobi_t<6>(W, V, batch, m, r, max_sweeps, flags, conv, sweeps_out, frob2, facc, sy, st);
@@ -661,14 +815,11 @@ void qr_apply_Q(const double* A, const double* tau, double* X, int batch, int m,
   if (batch == 0 || n == 0) return;
   ProfScope ps(PROF_QR, st, batch * 4.0 * m * n * k - 2.0 * batch * n * n * k, 8.0 * batch * (m * n + 2.0 * m * k),
                prof_tag("apply_q", batch, m, n, k));
-  CoopScratch& g_coop = ensure_coop(batch, st);
-  const int threads = 256;
-  int grid = coop_grid((const void*)apply_q_kernel, threads);
-  int64_t need = ((int64_t)batch * k + threads / 32 - 1) / (threads / 32);
-  grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, need));
-  Sync s{g_coop.bar, g_coop.abort, status, (long long)lim_spins()};
-  void* args[] = {&A, &tau, &X, &batch, &m, &n, &k, &strideA, &strideX, &s};
-  CTM_CUDA(cudaLaunchCooperativeKernel((const void*)apply_q_kernel, grid, threads, args, 0, st));
+  (void)status;
+  const int threads = 128;
+  const int64_t need = ((int64_t)batch * k + threads / 32 - 1) / (threads / 32);
+  apply_q_cols_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(need, 65535)), threads, 0, st>>>(
+      A, tau, X, batch, m, n, k, strideA, strideX);
   CTM_LAUNCHED();
 }
 

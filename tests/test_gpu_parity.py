@@ -1,6 +1,12 @@
 """CUDA path vs the FP64 oracle, element by element on the same seeded inputs (through the C ABI).
 
-Tolerances (FP64 mode): |dE/site| <= 1e-10 and gradient relative L2 <= 1e-5.
+Tolerances (FP64 mode): |dE/site| <= 1e-10 and gradient relative L2 <= 1e-5, except where the
+FP64 oracle cannot reproduce its own gradient that closely: at D=4, chi=32 after the workload's 40
+iterations the unrolled derivative through the first iterations (which start from a random
+environment whose spectra are graded over many decades) is ill-conditioned, and the oracle's
+gradient changes by 1e-4 (relative L2) when its SVD driver changes from LAPACK gesvd to gesdd while
+the energy changes by 1e-15.  There the energy keeps the 1e-10 bar and the gradient is held to
+1e-3, ten times the oracle's own spread.
 """
 import numpy as np
 import pytest
@@ -20,12 +26,12 @@ def test_heisenberg_d2_chi8_full_20_iterations():
     assert rel_l2(g, gr) <= 1e-5
 
 
-def test_heisenberg_d4_chi32_short():
+def test_heisenberg_d4_chi32_full_40_iterations():
     w = W.config("heis_d4_chi32")
-    E, g, _ = gpu_energy_grad(w, 4)
-    Er, gr = oracle_energy_grad(w, 4)
+    E, g, _ = gpu_energy_grad(w, w.n_iter)
+    Er, gr = oracle_energy_grad(w, w.n_iter)
     assert abs(E - Er) <= 1e-10, (E, Er)
-    assert rel_l2(g, gr) <= 1e-5
+    assert rel_l2(g, gr) <= 1e-3
 
 
 def test_shastry_sutherland_2x2_cell_small():
@@ -89,7 +95,7 @@ def test_batched_svd_entry_point():
 
 
 @pytest.mark.parametrize("tc_min", ["0", None])
-@pytest.mark.parametrize("name,n_iter", [("heis_d2_chi8", 20), ("heis_d4_chi32", 10)])
+@pytest.mark.parametrize("name,n_iter", [("heis_d2_chi8", 20), ("heis_d4_chi32", 40)])
 def test_mixed_tf32x3_matches_oracle(name, n_iter, tc_min, monkeypatch):
     # mixed mode: contractions in FP32 -- on the tensor cores (error-compensated TF32) above the size
     # threshold, which tc_min="0" lowers so that every eligible product takes tcgen05 -- and the
@@ -128,19 +134,19 @@ def test_plain_tf32_and_bf16_run_and_stay_close_in_energy(monkeypatch):
 
 def test_bf16x3_tensor_core_mode_runs_and_tracks_the_oracle(monkeypatch):
     # error-compensated BF16 (hi*hi + hi*lo + lo*hi, about 16 significant bits) with every
-    # eligible product forced onto the tcgen05 kernel: coarser than TF32x3, held to 1e-4
+    # eligible product forced onto the tcgen05 kernel: the mixed-mode bars on energy and gradient
     monkeypatch.setenv("CTM_TC_MIN_MNK", "0")
-    w = W.config("heis_d4_chi32")
-    n_iter = 10
+    w = W.config("heis_d2_chi8")
     ctm = make_ctm(w, "bf16x3")
     ctm.init(site_stack(w.tensors), env_flat(W.initial_environment(w)))
     ctm.profile(True)
-    e, _ = ctm.grad(n_iter)
+    e, dA = ctm.grad(w.n_iter)
     prof = ctm.profile_read()
     ctm.profile(False)
     assert prof["tc_gemm"][1] > 0
-    Er, _ = oracle_energy_grad(w, n_iter, grad=False)
-    assert abs(float(e[0]) - Er) <= 1e-4, (float(e[0]), Er)
+    Er, gr = oracle_energy_grad(w, w.n_iter)
+    assert abs(float(e[0]) - Er) <= 1e-6, (float(e[0]), Er)
+    assert rel_l2(dA.cpu().numpy().reshape(1, *w.tensors[0].shape), gr) <= 1e-3
 
 
 def test_strided_gemm_route_gives_identical_results(monkeypatch):

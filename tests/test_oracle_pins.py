@@ -372,3 +372,74 @@ def test_gradient_does_not_depend_on_the_svd_algorithm_at_the_cutoff():
     g2 = np.concatenate([x.ravel() for x in g2])
     assert abs(E1 - E2) < 1e-12
     assert np.linalg.norm(g1 - g2) / np.linalg.norm(g1) < 1e-6
+
+
+# ----------------------------------------------------------------------------- order parameters
+def test_one_site_rdm_of_the_nested_cluster_equals_the_state_vector():
+    # Eq. Mag1 needs one-site expectation values: the nested network with a single impurity Y,
+    # contracted exactly on an open cluster, against <psi|S_a|psi>/<psi|psi> from the amplitudes
+    from oracle.observables import SX, SZ, site_magnetization
+    rng = np.random.default_rng(13)
+    D, d, Lx, Ly = 2, 2, 3, 2
+    sites = [[torch.tensor(rng.standard_normal((d, D, D, D, D))) for _ in range(Lx)] for _ in range(Ly)]
+    psi = exact.state_vector(sites)
+    for y in range(Ly):
+        for x in range(Lx):
+            m = site_magnetization(exact.nested_site_rdm(sites, (x, y), d))
+            i = y * Lx + x
+            assert abs(m[0] - exact.site_expectation_sv(psi, SX, i)) < 1e-12
+            assert abs(m[2] - exact.site_expectation_sv(psi, SZ, i)) < 1e-12
+
+
+def test_magnetization_of_product_neel_and_dimer_states():
+    from oracle.observables import magnetization
+    from oracle.ctmrg import ctmrg
+    # D=1 product state: m = (v Sx v, 0, v Sz v) / |v|^2 exactly
+    v = np.array([0.8, -0.45])
+    A = torch.tensor(W.product_site(v))
+    grid = nested_cell([A], 1, 1)
+    env = ctmrg(grid, 4, 3, env=from_ring_arrays(_env0(1, 1, 1, 4), 2, 2))
+    m, M = magnetization([A], 1, 1, env, grid)
+    n2 = v @ v
+    assert np.abs(m[0] - np.array([v[0] * v[1] / n2, 0.0, 0.5 * (v[0] ** 2 - v[1] ** 2) / n2])).max() < 1e-12
+    assert abs(M - np.hypot(v[0] * v[1], 0.5 * (v[0] ** 2 - v[1] ** 2)) / n2) < 1e-12
+    # rotated Neel state: full moment 1/2
+    A = torch.tensor(W.neel_rotated_site())
+    grid = nested_cell([A], 1, 1)
+    env = ctmrg(grid, 4, 3, env=from_ring_arrays(_env0(1, 1, 1, 4), 2, 2))
+    assert abs(magnetization([A], 1, 1, env, grid)[1] - 0.5) < 1e-12
+    # dimer-singlet product state: every site is half of a singlet, so m_i = 0
+    As = [torch.tensor(a) for a in W.dimer_singlet_sites()]
+    grid = nested_cell(As, 2, 2)
+    env = ctmrg(grid, 8, 4, env=from_ring_arrays(_env0(2, 2, 2, 8), 4, 4))
+    m, M = magnetization(As, 2, 2, env, grid)
+    assert np.abs(m).max() < 1e-12 and M < 1e-12
+
+
+def test_plaquette_lists_are_the_empty_squares_of_the_cell():
+    # geometry of Eq. Mag2: the two lists partition the 8 nearest-neighbour bonds, each list is the
+    # boundary of one square, and neither square holds a J' dimer
+    terms = W.shastry_sutherland_terms()
+    a, b = W.shastry_sutherland_empty_plaquettes()
+    assert sorted(a + b) == list(range(8))
+
+    def square(px, py):
+        want = {(px % 2, py % 2, W.BOND_H), (px % 2, (py + 1) % 2, W.BOND_H),
+                (px % 2, py % 2, W.BOND_V), ((px + 1) % 2, py % 2, W.BOND_V)}
+        return sorted(k for k, t in enumerate(terms[:8]) if (t.x, t.y, t.kind) in want)
+
+    assert sorted(a) == square(1, 0) and sorted(b) == square(0, 1)
+    dimers = [(t.x, t.y, t.kind) for t in terms if t.kind in (W.BOND_DIAG_DR, W.BOND_DIAG_UR)]
+    assert dimers == [(0, 0, W.BOND_DIAG_DR), (1, 1, W.BOND_DIAG_UR)]   # inside squares (0,0), (1,1)
+
+
+def test_plaquette_order_of_the_dimer_state_and_by_hand():
+    from oracle.observables import plaquette_order
+    a, b = W.shastry_sutherland_empty_plaquettes()
+    vals = [0.1 * k for k in range(10)]
+    assert abs(plaquette_order(vals, a, b) - 0.25 * abs(sum(vals[k] for k in a) - sum(vals[k] for k in b))) < 1e-15
+    assert abs(plaquette_order(vals, a, b) - 0.25 * abs((0.2 + 0.6 + 0.3 + 0.1) - (0.4 + 0.0 + 0.5 + 0.7))) < 1e-15
+    sites = W.dimer_singlet_sites()
+    per = []
+    evaluate(sites, 2, 2, 8, 4, W.shastry_sutherland_terms(), env0=_env0(2, 2, 2, 8), grad=False, per_bond=per)
+    assert plaquette_order(per, a, b) < 1e-12

@@ -172,6 +172,19 @@ def shastry_sutherland_terms(J: float = 0.7, Jp: float = 1.0) -> list:
     return terms
 
 
+def shastry_sutherland_empty_plaquettes():
+    """Term indices (into ``shastry_sutherland_terms()``) of the two inequivalent empty plaquettes.
+
+    The squares of the 2x2 cell [A B; C F] are labelled by their upper-left site.  The squares at
+    (0, 0) and (1, 1) hold the J' dimers (A-F, and B-C of the neighbouring cells); the squares at
+    (1, 0) and (0, 1) are empty.  Square (px, py) has the bonds H(px, py), H(px, py+1), V(px, py)
+    and V(px+1, py), coordinates mod 2; with the term order H(x,y), V(x,y) for y, x in 0, 1:
+      square (1, 0): H(1,0)=2, H(1,1)=6, V(1,0)=3, V(0,0)=1
+      square (0, 1): H(0,1)=4, H(0,0)=0, V(0,1)=5, V(1,1)=7
+    """
+    return [2, 6, 3, 1], [4, 0, 5, 7]
+
+
 def config(name: str) -> Workload:
     """The seeded workloads: shapes of the paper's runs, random-normal tensors around a correlated core.
 

@@ -4,7 +4,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from .ctmrg import ctmrg, from_ring_arrays
+from .ctmrg import ctmrg, from_ring_arrays, to_ring_arrays
 from .energy import energy
 from .nested import DT, double_cell, nested_cell
 
@@ -30,6 +30,17 @@ def evaluate(As_np, Lx, Ly, chi, n_iter, terms, env0=None, grad=True, layer="nes
             return float(E.detach()), None
         E.backward()
     return float(E.detach()), [a.grad.numpy().copy() for a in As]
+
+
+def warm_environment(As_np, Lx, Ly, chi, n_iter, env0):
+    """The environment after ``n_iter`` CTMRG iterations (Fig. CTMRG) from ``env0``, returned
+    in the per-site ring convention of ``env0``.  The evaluations of an optimisation start from
+    such a pre-converged environment (the better initial value of the Discussion section)."""
+    As = [torch.tensor(np.asarray(a), dtype=DT) for a in As_np]
+    with torch.no_grad():
+        grid = nested_cell(As, Lx, Ly)
+        env = ctmrg(grid, chi, n_iter, env=from_ring_arrays(env0, len(grid), len(grid[0])))
+    return [[np.ascontiguousarray(a) for a in site] for site in to_ring_arrays(env)]
 
 
 def evaluate_workload(w, grad=True, n_iter=None, env0="default", **kw):

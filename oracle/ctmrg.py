@@ -44,6 +44,12 @@ Readings where the paper is silent:
   below the 1e-5 parity bar; at D=6, chi=64 it still keeps all 64 values.
 * Every updated C and T is divided by its Frobenius norm; the norm is held
   constant under differentiation (the energy does not depend on it).
+* Sign gauge of the singular triplets: each right singular vector of rho
+  (column of Q_s V) has its entry of largest magnitude (the first one on
+  ties) positive, and the left vector follows.  Energies and gradients do
+  not depend on it; it makes one CTMRG iteration a map with an element-wise
+  fixed point, which the fixed-point gradient (``oracle/fixed_point.py``)
+  needs.
 * Reverse mode of the projector step: the adjoint of the thin SVD of the
   bond density matrix rho = N S^t = (Q_n U) L (Q_s V)^t over its numerically
   non-zero singular values (s > RANK_TOL * s_1, RANK_TOL = 1e-13; those
@@ -109,6 +115,15 @@ def _svd(M: torch.Tensor):
     return torch.from_numpy(U), torch.from_numpy(s), torch.from_numpy(Vh.T.copy())
 
 
+def _sign_gauge(U: torch.Tensor, V: torch.Tensor, Qs: torch.Tensor):
+    """Flip (u_k, v_k) together so that the largest-magnitude entry of Q_s v_k is positive."""
+    Vp = Qs @ V
+    idx = Vp.abs().argmax(dim=0)
+    sg = torch.sign(Vp[idx, torch.arange(Vp.shape[1])])
+    sg = torch.where(sg == 0, torch.ones_like(sg), sg)
+    return U * sg, V * sg
+
+
 def _broadened_inverse_gaps(s: torch.Tensor, nz: torch.Tensor) -> torch.Tensor:
     """F_ij = (s_j^2 - s_i^2)/((s_j^2 - s_i^2)^2 + EPS (s_i^2 + s_j^2)^2) on the non-zero set, 0 elsewhere."""
     s2 = s * s
@@ -130,6 +145,7 @@ class Projectors(torch.autograd.Function):
         Qs, Rs = _qr(S)
         M = Rn @ Rs.T
         U, s, V = _svd(M)
+        U, V = _sign_gauge(U, V, Qs)
         k = s.shape[0]
         kept = min(chi, k)
         cut = CUTOFF * s[0]

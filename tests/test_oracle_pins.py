@@ -443,3 +443,64 @@ def test_plaquette_order_of_the_dimer_state_and_by_hand():
     per = []
     evaluate(sites, 2, 2, 8, 4, W.shastry_sutherland_terms(), env0=_env0(2, 2, 2, 8), grad=False, per_bond=per)
     assert plaquette_order(per, a, b) < 1e-12
+
+
+# ----------------------------------------------------------------------------- fixed-point gradient
+@pytest.fixture(scope="module")
+def _converged_d2():
+    from oracle.fixed_point import converge
+    w = W.config("heis_d2_chi8")
+    env, n, res = converge(w.tensors, w.Lx, w.Ly, w.chi, W.initial_environment(w), tol=1e-13)
+    assert res <= 1e-13
+    return w, env
+
+
+def test_sign_gauge_gives_an_elementwise_fixed_point(_converged_d2):
+    # with the projector SVD's sign gauge fixed, one more iteration reproduces the converged
+    # environment entry by entry (the premise of the fixed-point gradient)
+    from oracle.api import warm_environment
+    w, env = _converged_d2
+    nxt = warm_environment(w.tensors, w.Lx, w.Ly, w.chi, 1, env)
+    a = np.concatenate([x.ravel() for s in env for x in s])
+    b = np.concatenate([x.ravel() for s in nxt for x in s])
+    assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(a)
+
+
+def test_fixed_point_gradient_matches_finite_differences_of_the_converged_energy(_converged_d2):
+    # E(A) = e(A, env*(A)): every perturbed state is re-converged from env* to 1e-13, so the
+    # central difference is the derivative of the converged energy itself (not of a fixed
+    # number of iterations)
+    from oracle.fixed_point import converge, fixed_point_energy_grad
+    w, env = _converged_d2
+    E, g, n_adj, res = fixed_point_energy_grad(w.tensors, w.Lx, w.Ly, w.chi, w.terms, env)
+    assert res <= 1e-12 and n_adj < 200
+    A = w.tensors[0]
+    h = 1e-5
+    rng = np.random.default_rng(77)
+    idx = rng.choice(A.size, size=4, replace=False)
+    for k in idx:
+        vals = []
+        for sgn in (1, -1):
+            Ap = A.copy().ravel()
+            Ap[k] += sgn * h
+            Ap = Ap.reshape(A.shape)
+            envp, _, r = converge([Ap], w.Lx, w.Ly, w.chi, env, tol=1e-13, chunk=5)
+            assert r <= 1e-13
+            vals.append(evaluate([Ap], w.Lx, w.Ly, w.chi, 0, w.terms, env0=envp, grad=False)[0])
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(g[0].ravel()[k] - fd) <= 1e-6 * np.abs(g[0]).max(), (k, g[0].ravel()[k], fd)
+
+
+def test_fixed_point_gradient_is_the_limit_of_the_unrolled_one(_converged_d2):
+    # from the fixed point, the unrolled reverse mode over n iterations is the Neumann series cut
+    # after n terms: it approaches the fixed-point gradient as n grows; Euler's relation holds
+    from oracle.fixed_point import fixed_point_energy_grad
+    w, env = _converged_d2
+    E, g, _, _ = fixed_point_energy_grad(w.tensors, w.Lx, w.Ly, w.chi, w.terms, env)
+    errs = []
+    for n in (5, 40):
+        Eu, gu = evaluate(w.tensors, w.Lx, w.Ly, w.chi, n, w.terms, env0=env)
+        assert abs(Eu - E) <= 1e-13
+        errs.append(np.linalg.norm(gu[0] - g[0]) / np.linalg.norm(g[0]))
+    assert errs[1] <= 1e-7 and errs[1] < errs[0] / 100, errs
+    assert abs(np.sum(g[0] * w.tensors[0])) <= 1e-10 * np.linalg.norm(g[0]) * np.linalg.norm(w.tensors[0])

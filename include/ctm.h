@@ -64,7 +64,8 @@ enum {
   CTM_ERR_SVD_NOCONV = 5,   /* Jacobi SVD hit its sweep limit */
   CTM_ERR_DEGENERATE = 6,   /* all singular values of a bond density matrix are zero */
   CTM_ERR_TIMEOUT = 7,      /* a bounded device-side wait ran out */
-  CTM_ERR_STATE = 8         /* call out of order (e.g. ctm_step before ctm_init) */
+  CTM_ERR_STATE = 8,        /* call out of order (e.g. ctm_step before ctm_init) */
+  CTM_ERR_DIVERGED = 9      /* the fixed-point gradient's series grew instead of converging */
 };
 
 /* Arithmetic of the contractions.  QR, SVD, projectors, their adjoints and
@@ -133,6 +134,30 @@ int ctm_energy(ctm_handle* h, double* e_site_dev, double* e_bonds_dev, void* str
  * (recomputing each iteration from its stored environment).
  *   e_site_dev : device, 1 double.   dA_dev : device, FP64, layout of A. */
 int ctm_grad(ctm_handle* h, int n_iter, double* e_site_dev, double* dA_dev, void* stream);
+
+/* Fixed-point (implicit) gradient at the handle's current environment, which
+ * the caller has converged with ctm_step (the gradient from a converged
+ * environment proposed in the Discussion section, instead of the unrolled
+ * chain of Eq. AD).  With f one CTMRG iteration and e the energy (Eq. ExpH),
+ * at env* = f(A, env*):
+ *     dE/dA = de/dA + sum_{k>=0} [de/denv (df/denv)^k] df/dA,
+ * accumulated by repeated vector-Jacobian products through the one iteration
+ * recorded at env* (its projector factors computed once).  The series stops
+ * when a term adds less than tol relative to the running sum (tol <= 0 means
+ * 1e-10) or after max_terms terms (>= 1).
+ *   e_site_dev : device, 1 double: the energy at env*.
+ *   dA_dev     : device, FP64, layout of A.
+ *   info_host  : host, 2 doubles, or NULL: [0] terms taken, [1] fixed-point
+ *                residual ||f(A, env*) - env*|| / ||env*|| (how far the
+ *                environment is from a fixed point; the result is only as
+ *                good as this is small).
+ * Requires a prior ctm_init (CTM_ERR_STATE otherwise); the handle keeps env*.
+ * CTM_ERR_DIVERGED when a term grows past 10x the smallest term seen so far
+ * (the series diverges: env is not an attracting fixed point, e.g. not
+ * converged); info_host is filled in either case.
+ * Needs memory for one iteration's tape, not one per iteration. */
+int ctm_grad_fixed_point(ctm_handle* h, int max_terms, double tol, double* e_site_dev, double* dA_dev,
+                         double* info_host, void* stream);
 
 /* Order parameters of the current environment (Sec. Results).
  * ctm_magnetization: Eq. Mag1 for spin 1/2 (d = 2).  m_dev: device, Lx*Ly x 3 doubles, the

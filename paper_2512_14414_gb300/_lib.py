@@ -10,7 +10,7 @@ LIB_PATH = os.path.join(HERE, "libctm.so")
 CTM_FP64, CTM_TF32, CTM_BF16, CTM_TF32X3, CTM_BF16X3 = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": CTM_FP64, "tf32": CTM_TF32, "bf16": CTM_BF16, "tf32x3": CTM_TF32X3, "bf16x3": CTM_BF16X3}
 
-EXPORTS = ["ctm_create", "ctm_init", "ctm_step", "ctm_energy", "ctm_grad", "ctm_get_env", "ctm_set_env",
+EXPORTS = ["ctm_create", "ctm_init", "ctm_step", "ctm_energy", "ctm_grad", "ctm_grad_fixed_point", "ctm_get_env", "ctm_set_env",
            "ctm_env_numel", "ctm_kernel_launches", "ctm_set_limits", "ctm_magnetization", "ctm_plaquette_order", "ctm_profile", "ctm_profile_read", "ctm_svd", "ctm_svd_noalloc",
            "ctm_get_spectra", "ctm_mlp_forward", "ctm_destroy", "ctm_error_string"]
 PROF_CLASSES = {"gemm": 0, "permute": 1, "svd": 2, "qr": 3, "misc": 4, "tc_gemm": 5, "gemm_f64": 6}
@@ -45,6 +45,7 @@ def load():
     lib.ctm_step.argtypes = [vp, i, ctypes.POINTER(d), vp]
     lib.ctm_energy.argtypes = [vp, vp, vp, vp]
     lib.ctm_grad.argtypes = [vp, i, vp, vp, vp]
+    lib.ctm_grad_fixed_point.argtypes = [vp, i, d, vp, vp, ctypes.POINTER(d), vp]
     lib.ctm_get_env.argtypes = [vp, vp, vp]
     lib.ctm_set_env.argtypes = [vp, vp, vp]
     lib.ctm_env_numel.argtypes = [vp]

@@ -112,6 +112,18 @@ class CTM:
         _check(self.lib.ctm_grad(self.handle, int(n_iter), _ptr(e), _ptr(dA), _stream()), "ctm_grad")
         return e, dA
 
+    def grad_fixed_point(self, max_terms=200, tol=1e-10, dA=None, e=None):
+        """Fixed-point gradient at the current (converged) environment: (e, dA, terms, residual)."""
+        nA = self.Lx * self.Ly * self.d * self.D ** 4
+        dA = dA if dA is not None else torch.empty(self.Lx * self.Ly, self.d, self.D, self.D, self.D, self.D,
+                                                  dtype=torch.float64, device="cuda")
+        e = e if e is not None else torch.empty(1, dtype=torch.float64, device="cuda")
+        assert dA.numel() == nA
+        info = (ctypes.c_double * 2)()
+        _check(self.lib.ctm_grad_fixed_point(self.handle, int(max_terms), float(tol), _ptr(e), _ptr(dA), info,
+                                             _stream()), "ctm_grad_fixed_point")
+        return e, dA, int(info[0]), float(info[1])
+
     def set_limits(self, max_sweeps=0, spin_limit=0):
         """Sweep limit of the Jacobi SVD and spin limit of the bounded device waits (0: default)."""
         _check(self.lib.ctm_set_limits(self.handle, int(max_sweeps), int(spin_limit)), "ctm_set_limits")

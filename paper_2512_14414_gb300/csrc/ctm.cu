@@ -524,8 +524,20 @@ void projectors(ctm_handle* h, std::vector<PairIn>& in, std::vector<Tensor>& P, 
               h->cur_iter, h->cur_pair, h->cur_pair + nb - 1, r, sketched ? "sketch" : "full", l, sw, rk_floor, rk_cut,
               kept_list.c_str());
     }
-    // canonical signs keep the environment's chi basis fixed from one iteration to the next
-    for (int b = 0; b < nb; ++b) sign_fix(F[b]->U, F[b]->V, 1, in[b].n_r, F[b]->rs, st);
+    // Sign gauge of the singular triplets.  With the previous iteration's factors of the same pair at
+    // hand, each kept right vector takes the sign of its overlap with the previous one, so that a
+    // converged environment is reproduced entry by entry (the fixed point that ctm_grad_fixed_point
+    // differentiates); otherwise the entry of largest magnitude is made positive.  Both rules are
+    // locally constant, so the derivative ignores them.
+    for (int b = 0; b < nb; ++b) {
+      sign_fix(F[b]->U, F[b]->V, 1, in[b].n_r, F[b]->rs, st);
+      if (h->cur_iter >= 1 && (int)h->fac[h->cur_iter - 1].size() > h->cur_pair + b) {
+        const ctm_handle::Fac& pv = h->fac[h->cur_iter - 1][h->cur_pair + b];
+        if (pv.V && pv.n_r == in[b].n_r)
+          sign_align(F[b]->U, F[b]->V, F[b]->rs, pv.V, pv.rs, in[b].n_r,
+                     std::min<int>((int)chi, std::min(F[b]->rs, pv.rs)), st);
+      }
+    }
   }
   // P = S^t V' L^-1/2, Q = N^t U' L^-1/2 (identical in forward and replay)
   struct Saved {
@@ -1280,6 +1292,145 @@ int ctm_grad(ctm_handle* h, int n_iter, double* e_site_dev, double* dA_dev, void
   });
 }
 
+int ctm_grad_fixed_point(ctm_handle* h, int max_terms, double tol, double* e_site_dev, double* dA_dev,
+                         double* info_host, void* stream) {
+  if (!h || !e_site_dev || !dA_dev || max_terms < 1) return CTM_ERR_INVALID_ARG;
+  if (!h->inited) return CTM_ERR_STATE;
+  if (!(tol > 0.0)) tol = 1e-10;
+  return guard(h, [&]() {
+    using namespace ctm;
+    h->st = (cudaStream_t)stream;
+    Engine& E = *h->eng;
+    E.set_stream(h->st);
+    const int64_t nA = h->A64.numel();
+    const int64_t nenv = ctm_env_numel(h);
+    const int64_t per = (int64_t)h->d.d * h->d.D * h->d.D * h->d.D * h->d.D;
+    auto base = h->tape->mark();
+    // scratch: FP64 environment (for the residual), one series term of dA, norms, reduction work
+    double* envd = (double*)h->tape->alloc(sizeof(double) * nenv);
+    double* term = (double*)h->tape->alloc(sizeof(double) * nA);
+    double* nrm = (double*)h->tape->alloc(sizeof(double) * 8);
+    double* work = (double*)h->tape->alloc(sizeof(double) * 1024);
+    // one more iteration from env*, numbered after those already run so that its singular vectors
+    // take their signs from the previous iteration's: ckpt[it0] = env*, fac[it0] its factors
+    const int it0 = h->iters_done;
+    forward_iters(h, 1, nullptr);
+    // residual ||f(env*) - env*|| / ||env*||
+    for (int s = 0; s < h->nsites; ++s)
+      for (int k = 0; k < 8; ++k) h->env[s][k] = h->ckpt[it0][s][k];
+    save_env(h, envd);
+    sumsq(envd, F64, nenv, nrm + 3, work, h->st);
+    {
+      int64_t off = 0;
+      for (int s = 0; s < h->nsites; ++s)
+        for (int k = 0; k < 8; ++k) {
+          const Tensor& t = h->slots[s][k];
+          PermSpec ps;  // envd -= f(env*), tensor by tensor
+          ps.rank = 1;
+          ps.out_dims[0] = t.numel();
+          ps.in_stride[0] = 1;
+          permute(t.p, t.dt, envd + off, F64, ps, true, -1.0, h->st);
+          off += t.numel();
+        }
+    }
+    sumsq(envd, F64, nenv, nrm + 2, work, h->st);
+    // energy at env*: de/dA into dA, de/denv into denv
+    CTM_CUDA(cudaMemsetAsync(dA_dev, 0, nA * 8, h->st));
+    {
+      auto mark = h->tape->mark();
+      E.start_tape();
+      SiteLeaves sl = site_views(h, true);
+      g_sites = &sl;
+      for (int s = 0; s < h->nsites; ++s)
+        for (int k = 0; k < 8; ++k) h->env[s][k] = E.leaf(h->ckpt[it0][s][k]);
+      energy_op(h, e_site_dev, nullptr, true);
+      E.backward();
+      for (int p = 0; p < (int)sl.t.size(); ++p) {
+        void* g = E.grad(sl.t[p], false);
+        if (g) cast(g, h->edt, dA_dev + per * p, F64, per, true, h->st);
+      }
+      for (int s = 0; s < h->nsites; ++s)
+        for (int k = 0; k < 8; ++k) {
+          void* g = E.grad(h->env[s][k], false);
+          Tensor& dst = h->denv[s][k];
+          if (g)
+            CTM_CUDA(cudaMemcpyAsync(dst.p, g, dst.bytes(), cudaMemcpyDeviceToDevice, h->st));
+          else
+            CTM_CUDA(cudaMemsetAsync(dst.p, 0, dst.bytes(), h->st));
+        }
+      h->tape->release(mark);
+    }
+    // the series: each term replays iteration it0 from env* with its stored factors and pulls the
+    // environment cotangent back through it once
+    int terms = 0;
+    double hn[4] = {0.0, 0.0, 0.0, 0.0};
+    double smallest = -1.0;
+    bool diverged = false;
+    for (int n = 1; n <= max_terms; ++n) {
+      auto m2 = h->tape->mark();
+      E.start_tape();
+      SiteLeaves sl2 = site_views(h, true);
+      g_sites = &sl2;
+      std::vector<std::array<Tensor, 8>> leaves(h->nsites);
+      for (int s = 0; s < h->nsites; ++s)
+        for (int k = 0; k < 8; ++k) leaves[s][k] = h->env[s][k] = E.leaf(h->ckpt[it0][s][k]);
+      h->replay = true;
+      h->cur_iter = it0;
+      one_iteration(h);
+      h->replay = false;
+      for (int s = 0; s < h->nsites; ++s)
+        for (int k = 0; k < 8; ++k) E.seed_grad(h->env[s][k], h->denv[s][k].p, h->edt);
+      E.backward();
+      CTM_CUDA(cudaMemsetAsync(term, 0, nA * 8, h->st));
+      for (int p = 0; p < (int)sl2.t.size(); ++p) {
+        void* g = E.grad(sl2.t[p], false);
+        if (g) cast(g, h->edt, term + per * p, F64, per, true, h->st);
+      }
+      cast(term, F64, dA_dev, F64, nA, true, h->st);
+      for (int s = 0; s < h->nsites; ++s)
+        for (int k = 0; k < 8; ++k) {
+          void* g = E.grad(leaves[s][k], false);
+          Tensor& dst = h->denv[s][k];
+          if (g)
+            CTM_CUDA(cudaMemcpyAsync(dst.p, g, dst.bytes(), cudaMemcpyDeviceToDevice, h->st));
+          else
+            CTM_CUDA(cudaMemsetAsync(dst.p, 0, dst.bytes(), h->st));
+        }
+      h->tape->release(m2);
+      terms = n;
+      sumsq(term, F64, nA, nrm + 0, work, h->st);
+      sumsq(dA_dev, F64, nA, nrm + 1, work, h->st);
+      CTM_CUDA(cudaMemcpyAsync(hn, nrm, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      CTM_CUDA(cudaStreamSynchronize(h->st));
+      if (!std::isfinite(hn[0]) || !std::isfinite(hn[1])) {
+        diverged = true;
+        break;
+      }
+      if (hn[0] <= tol * tol * hn[1]) break;
+      if (smallest >= 0.0 && hn[0] > 100.0 * smallest) {  // |term| > 10 x the smallest |term|
+        diverged = true;
+        break;
+      }
+      if (smallest < 0.0 || hn[0] < smallest) smallest = hn[0];
+    }
+    g_sites = nullptr;
+    // leave the handle holding env*
+    for (int s = 0; s < h->nsites; ++s)
+      for (int k = 0; k < 8; ++k) {
+        Tensor& t = h->slots[s][k];
+        CTM_CUDA(cudaMemcpyAsync(t.p, h->ckpt[it0][s][k].p, t.bytes(), cudaMemcpyDeviceToDevice, h->st));
+        h->env[s][k] = t;
+      }
+    if (info_host) {
+      info_host[0] = terms;
+      info_host[1] = hn[3] > 0.0 ? std::sqrt(hn[2] / hn[3]) : 0.0;
+    }
+    h->tape->release(base);
+    sync_status(h);
+    if (diverged) throw Error(CTM_ERR_DIVERGED, "fixed-point gradient series diverged");
+  });
+}
+
 int ctm_get_env(ctm_handle* h, double* env_dev, void* stream) {
   if (!h || !env_dev) return CTM_ERR_INVALID_ARG;
   if (!h->inited) return CTM_ERR_STATE;
@@ -1505,6 +1656,7 @@ const char* ctm_error_string(int s) {
     case CTM_ERR_DEGENERATE: return "degenerate spectrum";
     case CTM_ERR_TIMEOUT: return "device wait timed out";
     case CTM_ERR_STATE: return "call out of order";
+    case CTM_ERR_DIVERGED: return "fixed-point gradient series diverged";
     default: return "unknown status";
   }
 }

@@ -1,4 +1,6 @@
 // Element-wise, permutation, SIMT GEMM, projector-helper and energy kernels of libctm.
+#include <type_traits>
+
 #include "kernels.h"
 
 #include <algorithm>
@@ -148,6 +150,66 @@ __global__ void permute_tiled(const Ti* __restrict__ in, To* __restrict__ out, P
   }
 }
 
+// Row copy: the innermost output dimension is contiguous in the input as well (in-stride 1), so
+// the permutation moves whole rows of `len` elements.  One warp per work item (a row, or a
+// 1024-element piece of a long one); the row's source and destination offsets are decoded once
+// and the piece is copied with 16-byte loads and stores where both ends are 16-byte aligned
+// (`vec` elements per access).
+struct PermRows {
+  int nouter;         // output dimensions before the row
+  int dims[7];        // their sizes
+  int64_t istr[7];    // their input strides
+  int64_t ostr[7];    // their output strides
+  int64_t nrows;
+  int len;            // row length (elements)
+  int chunk;          // elements per work item (a multiple of the vector width)
+  int nchunk;         // work items per row
+};
+
+template <typename Ti, typename To, bool ACC, int VEC>
+__global__ void permute_rows(const Ti* __restrict__ in, To* __restrict__ out, PermRows p, double scale) {
+  const int lane = threadIdx.x % 32;
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+  const int64_t items = p.nrows * p.nchunk;
+  for (int64_t item = gw; item < items; item += nw) {
+    const int64_t row = item / p.nchunk;
+    const int c0 = (int)(item % p.nchunk) * p.chunk;
+    const int c1 = min(p.len, c0 + p.chunk);
+    int64_t rem = row, ioff = 0, ooff = 0;
+    for (int k = p.nouter - 1; k >= 0; --k) {
+      const int64_t c = rem % p.dims[k];
+      rem /= p.dims[k];
+      ioff += c * p.istr[k];
+      ooff += c * p.ostr[k];
+    }
+    const Ti* src = in + ioff;
+    To* dst = out + ooff;
+    if (VEC > 1) {
+      // Ti == To here (no conversion), 16-byte vectors
+      using V = typename std::conditional<sizeof(Ti) == 8, double2, float4>::type;
+      const V* s4 = reinterpret_cast<const V*>(src);
+      V* d4 = reinterpret_cast<V*>(dst);
+      for (int i = c0 / VEC + lane; i < c1 / VEC; i += 32) {
+        V v = __ldg(s4 + i);
+        if (scale != 1.0 || ACC) {
+          Ti* e = reinterpret_cast<Ti*>(&v);
+          const Ti* o = reinterpret_cast<const Ti*>(d4 + i);
+#pragma unroll
+          for (int k = 0; k < VEC; ++k) e[k] = (Ti)(scale * (double)e[k] + (ACC ? (double)o[k] : 0.0));
+        }
+        d4[i] = v;
+      }
+    } else {
+      for (int i = c0 + lane; i < c1; i += 32) {
+        double v = scale * to_d(src[i]);
+        if (ACC) v += to_d(dst[i]);
+        dst[i] = from_d<To>(v);
+      }
+    }
+  }
+}
+
 template <typename Ti, typename To>
 void permute_t(const Ti* in, To* out, const PermSpec& ps, bool acc, double scale, cudaStream_t st) {
   int r = ps.rank;
@@ -165,6 +227,45 @@ void permute_t(const Ti* in, To* out, const PermSpec& ps, bool acc, double scale
   int b = -1;
   for (int k = 0; k < r - 1; ++k)
     if (ps.in_stride[k] == 1 && ps.out_dims[k] > 1) b = k;
+  // whole rows: the last output dimension is also contiguous in the input; merge with the
+  // dimensions before it while they stay contiguous in both
+  if (ps.in_stride[r - 1] == 1 && ps.out_dims[r - 1] >= 16) {
+    int64_t len = ps.out_dims[r - 1];
+    int k = r - 2;
+    while (k >= 0 && ps.in_stride[k] == len && len * ps.out_dims[k] < (int64_t(1) << 30)) len *= ps.out_dims[k--];
+    PermRows p{};
+    p.nouter = k + 1;
+    p.len = (int)len;
+    p.nrows = 1;
+    for (int q = 0; q <= k; ++q) {
+      p.dims[q] = (int)ps.out_dims[q];
+      p.istr[q] = ps.in_stride[q];
+      p.ostr[q] = ostr[q];
+      p.nrows *= ps.out_dims[q];
+    }
+    constexpr int vec = 16 / (int)sizeof(Ti);
+    // long rows are split into work items of 1024 elements (a warp moves 32 per access)
+    p.chunk = 1024;
+    p.nchunk = (int)((len + p.chunk - 1) / p.chunk);
+    const int64_t warps = p.nrows * p.nchunk;
+    const int bl = nblocks(warps, 8);
+    bool aligned = std::is_same<Ti, To>::value && sizeof(Ti) >= 4 && len % vec == 0 &&
+                   ((uintptr_t)in % 16) == 0 && ((uintptr_t)out % 16) == 0;
+    for (int q = 0; q <= k && aligned; ++q) aligned = (p.istr[q] % vec == 0) && (p.ostr[q] % vec == 0);
+    if (aligned) {
+      if (acc)
+        permute_rows<Ti, To, true, vec><<<bl, 256, 0, st>>>(in, out, p, scale);
+      else
+        permute_rows<Ti, To, false, vec><<<bl, 256, 0, st>>>(in, out, p, scale);
+    } else {
+      if (acc)
+        permute_rows<Ti, To, true, 1><<<bl, 256, 0, st>>>(in, out, p, scale);
+      else
+        permute_rows<Ti, To, false, 1><<<bl, 256, 0, st>>>(in, out, p, scale);
+    }
+    CTM_LAUNCHED();
+    return;
+  }
   bool tiled = r >= 2 && ps.in_stride[r - 1] != 1 && b >= 0 && ps.out_dims[r - 1] >= 8 && ps.out_dims[b] >= 8;
   if (tiled) {
     PermTile p{};
@@ -719,6 +820,22 @@ __global__ void sign_fix_k(double* U, double* V, int64_t n, int r) {
     }
 }
 
+// Sign gauge against a reference: column k of V (n x ld row-major, k < ncols) is flipped together
+// with U's column k when its overlap with column k of Vref (n x ldr row-major) is negative.
+__global__ void sign_align_k(double* U, double* V, int64_t ld, const double* Vref, int64_t ldr, int64_t n, int ncols) {
+  const int k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (k >= ncols) return;
+  double dot = 0.0;
+  for (int64_t i = lane; i < n; i += 32) dot = fma(V[i * ld + k], Vref[i * ldr + k], dot);
+  for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+  if (dot < 0.0)
+    for (int64_t i = lane; i < n; i += 32) {
+      V[i * ld + k] = -V[i * ld + k];
+      U[i * ld + k] = -U[i * ld + k];
+    }
+}
+
 __global__ void scale_cols_k(const double* Y, int64_t ldy, int64_t strideY, const double* s, int64_t strideS, double* X,
                              int64_t n, int kept) {
   const int b = blockIdx.y;
@@ -977,6 +1094,13 @@ void proj_prepare(const double* lam, double* U, double* V, double* inv, double* 
 void sign_fix(double* U, double* V, int batch, int64_t n, int r, cudaStream_t st) {
   dim3 grid((r + 7) / 8, batch);
   sign_fix_k<<<grid, 256, 0, st>>>(U, V, n, r);
+  CTM_LAUNCHED();
+}
+
+void sign_align(double* U, double* V, int64_t ld, const double* Vref, int64_t ldr, int64_t n, int ncols,
+                cudaStream_t st) {
+  if (ncols <= 0) return;
+  sign_align_k<<<(ncols + 7) / 8, 256, 0, st>>>(U, V, ld, Vref, ldr, n, ncols);
   CTM_LAUNCHED();
 }
 

@@ -74,6 +74,10 @@ void proj_prepare(const double* lam, double* U, double* V, double* inv, double* 
                   int64_t n_r, int r, int kept, double cut, double rank_tol, int* status, cudaStream_t st);
 // Sign gauge: column k of V (n x r row-major) gets a positive entry of largest magnitude; U follows.
 void sign_fix(double* U, double* V, int batch, int64_t n, int r, cudaStream_t st);
+// Flip (U[:,k], V[:,k]) for k < ncols where V[:,k] . Vref[:,k] < 0 (V, U: n x ld row-major, Vref:
+// n x ldr): aligns the sign gauge with a reference factorisation (the previous iteration's).
+void sign_align(double* U, double* V, int64_t ld, const double* Vref, int64_t ldr, int64_t n, int ncols,
+                cudaStream_t st);
 // X[b][i][k] = Y[b][i*ldy + k] * s[b][k] for k < kept (X is n x kept row-major)
 void scale_cols(const double* Y, int64_t ldy, int64_t strideY, const double* s, int64_t strideS, double* X,
                 int batch, int64_t n, int kept, cudaStream_t st);
@@ -124,8 +128,8 @@ void svd_sketch_product(const double* const* N, const double* const* S, const in
                         std::vector<int>& rank_host, cudaStream_t st);
 // Full thin SVD of rho_b = N_b S_b^t (n_r x n_r, rank <= r = min(n_r, n_l), the same r for the
 // whole batch): X = N S^t for n_r <= n_l, X = N R_s^t with S = Q_s R_s (Householder) for n_r > n_l,
-// so that rho = X B^t with B = I or Q_s.  X = Q_x R_x (Householder) and one-sided Jacobi on R_x^t:
-// R_x^t V_J = U_J S, hence U = Q_x V_J and V = B U_J.  Outputs per pair: lam (batch x r,
+// so that rho = X B^t with B = I or Q_s.  X = Q_x R_x, R_x^t = Q_2 R_2 (Householder) and one-sided
+// Jacobi on R_2^t: R_2^t V_J = U_J S, hence U = Q_x U_J and V = B Q_2 V_J.  Outputs per pair: lam (batch x r,
 // descending), U[b], V[b] (n_r x r row-major), rank_host[b] = values above 1e-14 lam_max.
 // ws: svd_product_full_ws(batch, max n_r, max n_l, r).
 size_t svd_product_full_ws(int batch, int nr, int nl, int r);

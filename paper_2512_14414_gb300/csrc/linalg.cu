@@ -937,9 +937,9 @@ void svd_sketch_product(const double* const* N, const double* const* S, const in
 }
 
 size_t svd_product_full_ws(int batch, int nr, int nl, int r) {
-  // Xc, Uc: batch x nr x r; Rx, Vw, Ul, Uo: batch x r x r; tall extras: Sc nr x nl, Qc nr x r, Rs r x r;
-  // reflector scalars of both QRs
-  const size_t per = (size_t)2 * nr * r + (size_t)4 * r * r + (size_t)nr * nl + (size_t)nr * r + (size_t)r * r + 2 * r;
+  // Xc, Uc: batch x nr x r; Rx, R2, Vw, Ul, Uo, Wt: batch x r x r; tall extras: Sc nr x nl, Qc nr x r,
+  // Rs r x r; reflector scalars of the three QRs
+  const size_t per = (size_t)2 * nr * r + (size_t)6 * r * r + (size_t)nr * nl + (size_t)nr * r + (size_t)r * r + 3 * r;
   return sizeof(double) * batch * per + sizeof(int) * 2 * batch + 256;
 }
 
@@ -955,16 +955,19 @@ void svd_product_full(const double* const* N, const double* const* S, const int*
   const int64_t Lr = (int64_t)nr * r, rr = (int64_t)r * r;
   double* Xc = ws;                    // X column-major (nr x r per pair; rows beyond n_r zero), then its QR
   double* Uc = Xc + batch * Lr;       // [V_J; 0] column-major, then U = Q_x [V_J; 0]
-  double* Rx = Uc + batch * Lr;       // R_x row-major = R_x^t column-major: the Jacobi working matrix
-  double* Vw = Rx + batch * rr;       // Jacobi rotation V_J, column-major
+  double* Rx = Uc + batch * Lr;       // R_x row-major = A = R_x^t column-major, then A's QR
+  double* R2 = Rx + batch * rr;       // R_2 row-major (A = Q_2 R_2) = R_2^t column-major: the Jacobi matrix
+  double* Vw = R2 + batch * rr;       // Jacobi rotation V_J, column-major
   double* Ul = Vw + batch * rr;       // sorted V_J, row-major
-  double* Uo = Ul + batch * rr;       // sorted left vectors of R_x^t (the rotation W of X), row-major
-  double* Sc = Uo + batch * rr;       // tall pairs: S column-major (n_r x n_l)
+  double* Uo = Ul + batch * rr;       // sorted U_J (normalised columns of R_2^t V_J), row-major
+  double* Wt = Uo + batch * rr;       // W = Q_2 V_J, column-major
+  double* Sc = Wt + batch * rr;       // tall pairs: S column-major (n_r x n_l)
   double* Qc = Sc + batch * (int64_t)nr * nl;  // tall pairs: Q_s column-major (n_r x r)
   double* Rs = Qc + batch * Lr;       // tall pairs: R_s row-major (r x r)
   double* taus = Rs + batch * rr;     // reflector scalars of S (tall pairs)
   double* taux = taus + batch * r;    // reflector scalars of X
-  int* inc = (int*)(taux + batch * r);
+  double* tau2 = taux + batch * r;    // reflector scalars of A = R_x^t
+  int* inc = (int*)(tau2 + batch * r);
   bool ragged = false;
   for (int b = 0; b < batch; ++b) ragged = ragged || nrs[b] != nr;
   if (ragged) CTM_CUDA(cudaMemsetAsync(Xc, 0, sizeof(double) * batch * Lr, st));
@@ -1012,33 +1015,40 @@ void svd_product_full(const double* const* N, const double* const* S, const int*
     g.M = mr; g.N = mr; g.K = ml; g.lda = ml; g.transB = true; g.ldb = ml; g.ldc = nr;
     gemm_f64(S[b], N[b], Xc + b * Lr, g, st);
   }
-  // X = Q_x R_x (Householder).  The one-sided Jacobi then runs on the r columns of R_x^t, i.e. on
-  // the rows of R_x: after the QR the graded spectrum sits on the diagonal and the sweeps converge
-  // in about a quarter of the sweeps they need on X itself (44 -> 11 on a 384-wide matrix graded
-  // over 13 decades).  R_x^t V_J = U_J S gives X = (Q_x V_J) S U_J^t.
+  // Preconditioning by two QR factorisations (as in Drmac and Veselic's one-sided Jacobi SVD):
+  // X = Q_x R_x, then A = R_x^t = Q_2 R_2, and the one-sided Jacobi runs on the r columns of R_2^t.
+  // After the QRs the graded spectrum sits on the diagonal and the sweeps converge in a fraction
+  // of the sweeps they need on X itself (44 -> 8 on a 384-wide matrix graded over 13 decades).
+  // R_2^t V_J = U_J S gives R_x = U_J S (Q_2 V_J)^t, hence X = (Q_x U_J) S (Q_2 V_J)^t.
   qr_householder(Xc, taux, batch, nr, r, Lr, status, st);
   qr_extract_R(Xc, Rx, batch, nr, r, Lr, st);
+  qr_householder(Rx, tau2, batch, r, r, rr, status, st);
+  qr_extract_R(Rx, R2, batch, r, r, rr, st);
   set_identity_colmajor(Vw, batch, r, st);
   CoopScratch& g_coop = ensure_coop(batch, st);
   CTM_CUDA(cudaMemsetAsync(g_coop.flags, 0, 3 * batch * sizeof(int), st));
   CTM_CUDA(cudaMemsetAsync(g_coop.conv, 0, batch * sizeof(int), st));
-  frob2_kernel<<<batch, 256, 0, st>>>(Rx, rr, g_coop.frob2);
+  frob2_kernel<<<batch, 256, 0, st>>>(R2, rr, g_coop.frob2);
   CTM_LAUNCHED();
   Sync sy{g_coop.bar, g_coop.abort, status, (long long)lim_spins()};
   {
     ProfScope ps(PROF_SVD, st, 0.0, 8.0 * batch * rr * 4, prof_tag("jacobi_full", batch, r, r, 0));
-    launch_jacobi(Rx, Vw, batch, r, r, lim_sweeps(), g_coop.flags, g_coop.conv, sweeps_out, g_coop.frob2,
+    launch_jacobi(R2, Vw, batch, r, r, lim_sweeps(), g_coop.flags, g_coop.conv, sweeps_out, g_coop.frob2,
                   g_coop.flop_acc, sy, st);
   }
   size_t smem = (size_t)r * (sizeof(double) + sizeof(int));
   if (smem > 48 * 1024)
     CTM_CUDA(cudaFuncSetAttribute(svd_rect_finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  // lam, Uo = U_J (normalised columns of R_x^t V_J, sorted), Ul = V_J sorted
-  svd_rect_finalize_kernel<<<batch, 256, smem, st>>>(Rx, Vw, lam, r, Uo, r, Ul, r, r, inc, inc + batch, status);
+  // lam, Uo = U_J (normalised columns of R_2^t V_J, sorted), Ul = V_J sorted
+  svd_rect_finalize_kernel<<<batch, 256, smem, st>>>(R2, Vw, lam, r, Uo, r, Ul, r, r, inc, inc + batch, status);
   CTM_LAUNCHED();
-  // U = Q_x [V_J; 0]
-  for (int b = 0; b < batch; ++b) embed_transpose(Ul + b * rr, r, Uc + b * Lr, nr, st);
+  // U = Q_x [U_J; 0] and W = Q_2 V_J (both column-major)
+  for (int b = 0; b < batch; ++b) {
+    embed_transpose(Uo + b * rr, r, Uc + b * Lr, nr, st);
+    embed_transpose(Ul + b * rr, r, Wt + b * rr, r, st);
+  }
   qr_apply_Q(Xc, taux, Uc, batch, nr, r, r, Lr, Lr, status, st);
+  qr_apply_Q(Rx, tau2, Wt, batch, r, r, r, rr, rr, status, st);
   for (int b = 0; b < batch; ++b) {
     const int mr = nrs[b];
     PermSpec ps;  // row-major n_r x r from the column-major block (first n_r rows)
@@ -1049,12 +1059,18 @@ void svd_product_full(const double* const* N, const double* const* S, const int*
     ps.in_stride[1] = nr;
     permute(Uc + b * Lr, F64, U[b], F64, ps, false, 1.0, st);
     if (mr <= nls[b]) {
-      CTM_CUDA(cudaMemcpyAsync(V[b], Uo + b * rr, sizeof(double) * rr, cudaMemcpyDeviceToDevice, st));
+      PermSpec pw;  // V = W (row-major r x r)
+      pw.rank = 2;
+      pw.out_dims[0] = r;
+      pw.out_dims[1] = r;
+      pw.in_stride[0] = 1;
+      pw.in_stride[1] = r;
+      permute(Wt + b * rr, F64, V[b], F64, pw, false, 1.0, st);
     } else {
-      // V = Q_s U_J (Q_s column-major n_r x r)
+      // V = Q_s W (Q_s column-major n_r x r, W column-major r x r)
       g = GemmSpec();
-      g.M = mr; g.N = r; g.K = r; g.transA = true; g.lda = mr; g.ldb = r; g.ldc = r;
-      gemm_f64(Qc + b * Lr, Uo + b * rr, V[b], g, st);
+      g.M = mr; g.N = r; g.K = r; g.transA = true; g.lda = mr; g.transB = true; g.ldb = r; g.ldc = r;
+      gemm_f64(Qc + b * Lr, Wt + b * rr, V[b], g, st);
     }
   }
   std::vector<int> flags(2 * batch, 0);

@@ -154,23 +154,45 @@ def lbfgs(fun: Fun, x0: np.ndarray, m: int = 10, max_iter: int = 20, gtol: float
     return res
 
 
-def optimize_peps(ctm, A0: np.ndarray, env0, n_iter: int, max_steps: int = 20, m: int = 10, callback=None):
-    """L-BFGS on the site tensors of a PEPS with the GPU energy and gradient (``CTM.grad``).
+def optimize_peps(ctm, A0: np.ndarray, env0, n_iter: int, max_steps: int = 20, m: int = 10, callback=None,
+                  gradient: str = "unrolled", conv_tol: float = 1e-10, max_ctm: int = 400):
+    """L-BFGS on the site tensors of a PEPS with the GPU energy and gradient.
 
-    ``A0``: (Lx*Ly, d, D, D, D, D) FP64 host array; ``env0``: the initial environment (device
-    FP64 tensor, re-used at every evaluation so that E(X) is one fixed function).
+    ``A0``: (Lx*Ly, d, D, D, D, D) FP64 host array; ``env0``: the initial environment (device FP64).
+    ``gradient="unrolled"``: every evaluation runs ``n_iter`` iterations from ``env0`` and
+    differentiates through all of them (``CTM.grad``), so E(X) is one fixed function.
+    ``gradient="fixed_point"``: every evaluation starts from the environment the previous one
+    converged (the first from ``env0``), iterates until the spectrum change of an iteration is at
+    most ``conv_tol`` (at most ``max_ctm`` iterations) and takes the fixed-point gradient of the
+    converged energy (``CTM.grad_fixed_point``); E(X) is then the converged energy, defined up to
+    the convergence tolerance.
     """
     import torch
 
     shape = A0.shape
     dev = env0.device
+    state = {"env": env0}
 
-    def fun(x):
+    def fun_unrolled(x):
         A = torch.from_numpy(x.reshape(shape)).to(dev)
         ctm.init(A, env0)
         e, dA = ctm.grad(n_iter)
         return float(e[0]), dA.detach().cpu().numpy().ravel()
 
+    def fun_fixed_point(x):
+        A = torch.from_numpy(x.reshape(shape)).to(dev)
+        ctm.init(A, state["env"])
+        done = 0
+        while done < max_ctm:
+            delta = ctm.step(5)
+            done += 5
+            if 0.0 <= delta <= conv_tol:
+                break
+        e, dA, _, _ = ctm.grad_fixed_point(tol=max(conv_tol, 1e-10))
+        state["env"] = ctm.get_env().clone()
+        return float(e[0]), dA.detach().cpu().numpy().ravel()
+
+    fun = fun_fixed_point if gradient == "fixed_point" else fun_unrolled
     return lbfgs(fun, A0.ravel(), m=m, max_iter=max_steps, callback=callback)
 
 
@@ -191,6 +213,10 @@ def main():
     ap.add_argument("--history", type=int, default=10)
     ap.add_argument("--precision", default="tf32x3")
     ap.add_argument("--n-iter", type=int, default=None)
+    ap.add_argument("--gradient", default="unrolled", choices=["unrolled", "fixed_point"])
+    ap.add_argument("--conv-tol", type=float, default=None,
+                    help="spectrum-change tolerance of the fixed-point evaluations (default 1e-10 in FP64, "
+                         "1e-6 in the mixed modes)")
     args = ap.parse_args()
     w = W.config(args.workload)
     n_iter = args.n_iter or w.n_iter
@@ -204,9 +230,11 @@ def main():
         print(json.dumps({"step": res.n_iter, "energy": res.f, "grad_norm": float(np.linalg.norm(res.g)),
                           "evaluations": res.n_eval, "elapsed_s": time.perf_counter() - t0}), flush=True)
 
+    conv_tol = args.conv_tol if args.conv_tol is not None else (1e-10 if args.precision == "fp64" else 1e-6)
     res = optimize_peps(ctm, np.stack(w.tensors), env0, n_iter, max_steps=args.steps, m=args.history,
-                        callback=report)
-    print(json.dumps({"workload": w.name, "precision": args.precision, "n_iter": n_iter, "steps": res.n_iter,
+                        callback=report, gradient=args.gradient, conv_tol=conv_tol)
+    print(json.dumps({"workload": w.name, "precision": args.precision, "gradient": args.gradient,
+                      "n_iter": n_iter, "steps": res.n_iter,
                       "energy_start": res.history[0], "energy_end": res.f, "evaluations": res.n_eval,
                       "message": res.message, "elapsed_s": time.perf_counter() - t0}), flush=True)
 

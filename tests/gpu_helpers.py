@@ -1,4 +1,6 @@
 """Shared set-up of the GPU tests: seeded inputs in the layouts of include/ctm.h."""
+import functools
+
 import numpy as np
 import torch
 
@@ -32,6 +34,20 @@ def oracle_energy_grad(w, n_iter, env0=None, grad=True):
     from oracle.api import evaluate
     env0 = W.initial_environment(w) if env0 is None else env0
     return evaluate(w.tensors, w.Lx, w.Ly, w.chi, n_iter, w.terms, env0=env0, grad=grad)
+
+
+@functools.lru_cache(maxsize=4)
+def _warm(name, n_warm):
+    from oracle.api import warm_environment
+    w = W.config(name)
+    return warm_environment(w.tensors, w.Lx, w.Ly, w.chi, n_warm, W.initial_environment(w))
+
+
+def oracle_warm_env(w, n_warm):
+    """The environment the oracle reaches after ``n_warm`` iterations from the workload's seeded
+    random environment: the pre-converged start of an evaluation inside an optimisation.  Both
+    sides then evaluate from it, so the input comes from the oracle, never from the CUDA path."""
+    return _warm(w.name, n_warm)
 
 
 def rel_l2(a, b):

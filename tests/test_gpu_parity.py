@@ -1,19 +1,19 @@
 """CUDA path vs the FP64 oracle, element by element on the same seeded inputs (through the C ABI).
 
-Tolerances (FP64 mode): |dE/site| <= 1e-10 and gradient relative L2 <= 1e-5, except where the
-FP64 oracle cannot reproduce its own gradient that closely: at D=4, chi=32 after the workload's 40
-iterations the unrolled derivative through the first iterations (which start from a random
-environment whose spectra are graded over many decades) is ill-conditioned, and the oracle's
-gradient changes by 1e-4 (relative L2) when its SVD driver changes from LAPACK gesvd to gesdd while
-the energy changes by 1e-15.  There the energy keeps the 1e-10 bar and the gradient is held to
-1e-3, ten times the oracle's own spread.
+Tolerances: |dE/site| <= 1e-10 and gradient relative L2 <= 1e-5 in FP64 mode, 1e-6 and 1e-3 in the
+mixed modes.  Where the workload's iteration count is long (D=4, chi=32, 40 iterations), the
+evaluation starts from a pre-converged environment that the oracle prepares (40 iterations from the
+seeded random environment), as every evaluation after the first one of an optimisation does.  From
+the random environment itself the unrolled derivative through the first iterations is
+ill-conditioned: there the oracle's own gradient moves by 1e-4 (relative L2) when its SVD driver
+changes from LAPACK gesvd to gesdd, against 7e-9 from the pre-converged start.
 """
 import numpy as np
 import pytest
 import torch
 
 import workloads as W
-from gpu_helpers import env_flat, gpu_energy_grad, make_ctm, oracle_energy_grad, rel_l2, site_stack
+from gpu_helpers import env_flat, gpu_energy_grad, make_ctm, oracle_energy_grad, oracle_warm_env, rel_l2, site_stack
 
 pytestmark = pytest.mark.gpu
 
@@ -26,12 +26,13 @@ def test_heisenberg_d2_chi8_full_20_iterations():
     assert rel_l2(g, gr) <= 1e-5
 
 
-def test_heisenberg_d4_chi32_full_40_iterations():
+def test_heisenberg_d4_chi32_full_40_iterations_from_a_preconverged_environment():
     w = W.config("heis_d4_chi32")
-    E, g, _ = gpu_energy_grad(w, w.n_iter)
-    Er, gr = oracle_energy_grad(w, w.n_iter)
+    env0 = oracle_warm_env(w, w.n_iter)
+    E, g, _ = gpu_energy_grad(w, w.n_iter, env0=env0)
+    Er, gr = oracle_energy_grad(w, w.n_iter, env0=env0)
     assert abs(E - Er) <= 1e-10, (E, Er)
-    assert rel_l2(g, gr) <= 1e-3
+    assert rel_l2(g, gr) <= 1e-5, rel_l2(g, gr)
 
 
 def test_shastry_sutherland_2x2_cell_small():
@@ -95,18 +96,19 @@ def test_batched_svd_entry_point():
 
 
 @pytest.mark.parametrize("tc_min", ["0", None])
-@pytest.mark.parametrize("name,n_iter", [("heis_d2_chi8", 20), ("heis_d4_chi32", 40)])
-def test_mixed_tf32x3_matches_oracle(name, n_iter, tc_min, monkeypatch):
+@pytest.mark.parametrize("name,n_warm", [("heis_d2_chi8", 0), ("heis_d4_chi32", 40)])
+def test_mixed_tf32x3_matches_oracle(name, n_warm, tc_min, monkeypatch):
     # mixed mode: contractions in FP32 -- on the tensor cores (error-compensated TF32) above the size
     # threshold, which tc_min="0" lowers so that every eligible product takes tcgen05 -- and the
-    # decompositions in FP64
+    # decompositions in FP64; the workload's iteration count, from the pre-converged environment at D=4
     if tc_min is not None:
         monkeypatch.setenv("CTM_TC_MIN_MNK", tc_min)
     w = W.config(name)
-    E, g, _ = gpu_energy_grad(w, n_iter, precision="tf32x3")
-    Er, gr = oracle_energy_grad(w, n_iter)
+    env0 = oracle_warm_env(w, n_warm) if n_warm else None
+    E, g, _ = gpu_energy_grad(w, w.n_iter, precision="tf32x3", env0=env0)
+    Er, gr = oracle_energy_grad(w, w.n_iter, env0=env0)
     assert abs(E - Er) <= 1e-6, (E, Er)
-    assert rel_l2(g, gr) <= 1e-3
+    assert rel_l2(g, gr) <= 1e-3, rel_l2(g, gr)
 
 
 def test_tensor_core_route_runs_when_forced(monkeypatch):

@@ -152,9 +152,11 @@ int ctm_grad(ctm_handle* h, int n_iter, double* e_site_dev, double* dA_dev, void
  *                environment is from a fixed point; the result is only as
  *                good as this is small).
  * Requires a prior ctm_init (CTM_ERR_STATE otherwise); the handle keeps env*.
- * CTM_ERR_DIVERGED when a term grows past 10x the smallest term seen so far
- * (the series diverges: env is not an attracting fixed point, e.g. not
- * converged); info_host is filled in either case.
+ * The series also stops when its terms have reached a rounding floor (no new
+ * smallest term for 10 terms, each below 1e-4 of the sum).
+ * CTM_ERR_DIVERGED when a term grows past 10x the first term (the series
+ * diverges: env* is not an attracting fixed point, e.g. the iteration has
+ * not converged or cycles); info_host is filled in either case.
  * Needs memory for one iteration's tape, not one per iteration. */
 int ctm_grad_fixed_point(ctm_handle* h, int max_terms, double tol, double* e_site_dev, double* dA_dev,
                          double* info_host, void* stream);

@@ -68,6 +68,7 @@ struct Profiler {
   std::vector<double> flops, bytes;
   std::vector<std::string> tags;  // per launch, only when dumping
   size_t used = 0;
+  int depth = 0;  // nested scopes count toward the outermost one only
   double ms[PROF_NCLASS] = {0}, fl[PROF_NCLASS] = {0}, by[PROF_NCLASS] = {0};
   int64_t n[PROF_NCLASS] = {0};
   FILE* dump = nullptr;  // per-launch records (CTM_PROF_DUMP=<path>): class, tag, ms

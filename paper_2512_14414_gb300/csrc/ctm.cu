@@ -1364,7 +1364,8 @@ int ctm_grad_fixed_point(ctm_handle* h, int max_terms, double tol, double* e_sit
     // environment cotangent back through it once
     int terms = 0;
     double hn[4] = {0.0, 0.0, 0.0, 0.0};
-    double smallest = -1.0;
+    double first = -1.0, smallest = -1.0;
+    int stalled = 0;
     bool diverged = false;
     for (int n = 1; n <= max_terms; ++n) {
       auto m2 = h->tape->mark();
@@ -1407,11 +1408,19 @@ int ctm_grad_fixed_point(ctm_handle* h, int max_terms, double tol, double* e_sit
         break;
       }
       if (hn[0] <= tol * tol * hn[1]) break;
-      if (smallest >= 0.0 && hn[0] > 100.0 * smallest) {  // |term| > 10 x the smallest |term|
+      if (first < 0.0) first = hn[0];
+      if (hn[0] > 100.0 * first) {  // |term| > 10 x |first term|: the series grows
         diverged = true;
         break;
       }
-      if (smallest < 0.0 || hn[0] < smallest) smallest = hn[0];
+      // rounding floor: no new smallest term for 10 terms while the terms are already 1e-4 of the
+      // sum (the mixed modes converge the environment only to FP32 rounding)
+      if (smallest < 0.0 || hn[0] < smallest) {
+        smallest = hn[0];
+        stalled = 0;
+      } else if (++stalled >= 10 && hn[0] <= 1e-8 * hn[1]) {
+        break;
+      }
     }
     g_sites = nullptr;
     // leave the handle holding env*

@@ -14,6 +14,7 @@ thread_local Profiler* g_prof = nullptr;
 thread_local const Limits* g_limits = nullptr;
 
 void Profiler::begin(int c, cudaStream_t st, double f, double b, const char* tag) {
+  if (depth++ > 0) return;
   if (used + 2 > ev.size()) {
     if (ev.size() >= (size_t(1) << 16)) fold();
     if (used + 2 > ev.size()) {
@@ -30,6 +31,7 @@ void Profiler::begin(int c, cudaStream_t st, double f, double b, const char* tag
 }
 
 void Profiler::end(cudaStream_t st) {
+  if (--depth > 0) return;
   if (used % 2 == 1) cudaEventRecord(ev[used++], st);
 }
 
@@ -55,6 +57,7 @@ void Profiler::fold() {
 
 void Profiler::clear() {
   used = 0;
+  depth = 0;
   cls.clear();
   flops.clear();
   bytes.clear();

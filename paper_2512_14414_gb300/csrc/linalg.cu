@@ -147,6 +147,151 @@ __global__ void apply_q_cols_kernel(const double* A, const double* tau, double* 
   }
 }
 
+// ---- register-resident variants (m <= 32 * MAXE): a warp holds a whole column in registers, lane l
+// owning rows l + 32 e, so that each reflector step issues all of its loads at once instead of one
+// L2 round trip per element.
+
+template <int MAXE>
+__device__ __forceinline__ void load_col_r(const double* col, int m, int lane, double (&x)[MAXE]) {
+#pragma unroll
+  for (int e = 0; e < MAXE; ++e) {
+    const int i = lane + 32 * e;
+    x[e] = i < m ? __ldcg(col + i) : 0.0;
+  }
+}
+
+template <int MAXE>
+__device__ __forceinline__ void store_col_r(double* col, int m, int lane, const double (&x)[MAXE]) {
+#pragma unroll
+  for (int e = 0; e < MAXE; ++e) {
+    const int i = lane + 32 * e;
+    if (i < m) col[i] = x[e];
+  }
+}
+
+// x -= tau v (v . x) with v = (.., 1 at row j, A[j+1:, j]) given in registers (rows > j of vcol).
+template <int MAXE>
+__device__ __forceinline__ void reflect_r(double (&x)[MAXE], const double (&v)[MAXE], double tj, int j, int lane) {
+  double w = 0.0;
+#pragma unroll
+  for (int e = 0; e < MAXE; ++e) {
+    const int i = lane + 32 * e;
+    w = (i > j) ? fma(v[e], x[e], w) : (i == j ? w + x[e] : w);
+  }
+  w = warp_sum(w) * tj;
+#pragma unroll
+  for (int e = 0; e < MAXE; ++e) {
+    const int i = lane + 32 * e;
+    x[e] = (i > j) ? fma(-w, v[e], x[e]) : (i == j ? x[e] - w : x[e]);
+  }
+}
+
+// Reflector of the column in registers at row j (the column is column j of the matrix): rows > j
+// become v[1:], row j becomes beta; returns tau.
+template <int MAXE>
+__device__ __forceinline__ double make_reflector_r(double (&x)[MAXE], int j, int lane) {
+  double alpha = 0.0, s = 0.0;
+#pragma unroll
+  for (int e = 0; e < MAXE; ++e) {
+    const int i = lane + 32 * e;
+    if (i == j) alpha = x[e];
+    if (i > j) s = fma(x[e], x[e], s);
+  }
+  alpha = warp_sum(alpha);  // only the owning lane contributes
+  s = warp_sum(s);
+  if (!(s > 0.0)) return 0.0;
+  const double beta = -copysign(sqrt(alpha * alpha + s), alpha);
+  const double t = (beta - alpha) / beta;
+  const double sc = 1.0 / (alpha - beta);
+#pragma unroll
+  for (int e = 0; e < MAXE; ++e) {
+    const int i = lane + 32 * e;
+    if (i > j) x[e] *= sc;
+    if (i == j) x[e] = beta;
+  }
+  return t;
+}
+
+template <int MAXE>
+__global__ void qr_kernel_r(double* A, double* tau, int batch, int m, int n, int64_t strideA, Sync s) {
+  const int lane = threadIdx.x % 32;
+  const int wpb = blockDim.x / 32;
+  const int64_t gw = (int64_t)blockIdx.x * wpb + threadIdx.x / 32;
+  const int64_t nw = (int64_t)gridDim.x * wpb;
+  for (int64_t b = gw; b < batch; b += nw) {
+    double x[MAXE];
+    load_col_r<MAXE>(A + b * strideA, m, lane, x);
+    const double t = make_reflector_r<MAXE>(x, 0, lane);
+    store_col_r<MAXE>(A + b * strideA, m, lane, x);
+    if (lane == 0) tau[b * n] = t;
+  }
+  for (int j = 0; j < n - 1; ++j) {
+    if (!grid_barrier(s)) return;
+    const int64_t ncols = n - j - 1;
+    const int64_t tasks = (int64_t)batch * ncols;
+    for (int64_t t = gw; t < tasks; t += nw) {
+      const int64_t b = t / ncols;
+      const int c = j + 1 + (int)(t % ncols);
+      double* Ab = A + b * strideA;
+      double x[MAXE], v[MAXE];
+      load_col_r<MAXE>(Ab + (int64_t)c * m, m, lane, x);
+      load_col_r<MAXE>(Ab + (int64_t)j * m, m, lane, v);
+      const double tj = __ldcg(tau + b * n + j);
+      if (tj != 0.0) reflect_r<MAXE>(x, v, tj, j, lane);
+      if (c == j + 1) {
+        const double tn = make_reflector_r<MAXE>(x, j + 1, lane);
+        if (lane == 0) tau[b * n + j + 1] = tn;
+      }
+      store_col_r<MAXE>(Ab + (int64_t)c * m, m, lane, x);
+    }
+  }
+}
+
+// X := Q X with the column of X in registers through all n reflectors.
+template <int MAXE>
+__global__ void apply_q_cols_kernel_r(const double* A, const double* tau, double* X, int batch, int m, int n, int k,
+                                      int64_t strideA, int64_t strideX) {
+  const int lane = threadIdx.x % 32;
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+  const int64_t tasks = (int64_t)batch * k;
+  for (int64_t t = gw; t < tasks; t += nw) {
+    const int64_t b = t / k;
+    const int c = (int)(t % k);
+    double* xc = X + b * strideX + (int64_t)c * m;
+    double x[MAXE];
+    load_col_r<MAXE>(xc, m, lane, x);
+    for (int j = n - 1; j >= 0; --j) {
+      const double tj = __ldg(tau + b * n + j);
+      if (tj == 0.0) continue;
+      double v[MAXE];
+      load_col_r<MAXE>(A + b * strideA + (int64_t)j * m, m, lane, v);
+      reflect_r<MAXE>(x, v, tj, j, lane);
+    }
+    store_col_r<MAXE>(xc, m, lane, x);
+  }
+}
+
+// FP32 copy of a batch of r x r matrices scaled to unit Frobenius norm, and an FP32 identity.
+__global__ void to_f32_unit_kernel(const double* W, float* W32, float* V32, int r, const double* frob2) {
+  const int b = blockIdx.y;
+  const int64_t rr = (int64_t)r * r;
+  const double sc = 1.0 / sqrt(frob2[b]);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < rr; e += (int64_t)gridDim.x * blockDim.x) {
+    W32[b * rr + e] = (float)(W[b * rr + e] * sc);
+    V32[b * rr + e] = (e / r == e % r) ? 1.0f : 0.0f;
+  }
+}
+
+__global__ void f32_to_f64_kernel(const float* x, double* y, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = (double)x[e];
+}
+
+__global__ void fill_kernel(double* x, int64_t n, double v) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) x[e] = v;
+}
+
 __global__ void extract_r_kernel(const double* A, double* R, int m, int n, int64_t strideA) {
   const int b = blockIdx.y;
   int64_t total = (int64_t)n * n;
@@ -438,11 +583,11 @@ __global__ void __launch_bounds__(128) jacobi_team_kernel(double* W, double* V, 
 // sums, and no block-wide synchronisation separates the load, the test and the rotation.  A round
 // is then bound by the FP64 pipes of the SMs rather than by block barriers, and a quarter as many
 // blocks meet at each grid barrier.  Requires max(m, r) <= 32 * MAXE.
-template <int MAXE>
-__global__ void __launch_bounds__(128) jacobi_warp_kernel(double* W, double* V, int batch, int m, int r, int rp,
+template <typename T, int MAXE>
+__global__ void __launch_bounds__(128) jacobi_warp_kernel(T* W, T* V, int batch, int m, int r, int rp,
                                                            int max_sweeps, double tol, int* flags, int* conv,
                                                            int* sweeps_out, const double* frob2, double* flop_acc,
-                                                           Sync s) {
+                                                           Sync s, int report_noconv) {
   const int t = threadIdx.x, lane = t % 32;
   const int wpb = blockDim.x / 32;
   const int64_t gw = (int64_t)blockIdx.x * wpb + t / 32;
@@ -466,20 +611,20 @@ __global__ void __launch_bounds__(128) jacobi_warp_kernel(double* W, double* V, 
         int p, q;
         rr_pair(round, (int)(task % npairs), rp, p, q);
         if (p >= r || q >= r) continue;
-        double* ap = W + b * mr + (int64_t)p * m;
-        double* aq = W + b * mr + (int64_t)q * m;
-        double* vp = V + b * rr + (int64_t)p * r;
-        double* vq = V + b * rr + (int64_t)q * r;
-        double x[MAXE], y[MAXE], u[MAXE], w[MAXE];
+        T* ap = W + b * mr + (int64_t)p * m;
+        T* aq = W + b * mr + (int64_t)q * m;
+        T* vp = V + b * rr + (int64_t)p * r;
+        T* vq = V + b * rr + (int64_t)q * r;
+        T x[MAXE], y[MAXE], u[MAXE], w[MAXE];
 #pragma unroll
         for (int e = 0; e < MAXE; ++e) {
           const int i = lane + 32 * e;
-          x[e] = i < m ? __ldcg(ap + i) : 0.0;
-          y[e] = i < m ? __ldcg(aq + i) : 0.0;
-          u[e] = i < r ? __ldcg(vp + i) : 0.0;
-          w[e] = i < r ? __ldcg(vq + i) : 0.0;
+          x[e] = i < m ? __ldcg(ap + i) : T(0);
+          y[e] = i < m ? __ldcg(aq + i) : T(0);
+          u[e] = i < r ? __ldcg(vp + i) : T(0);
+          w[e] = i < r ? __ldcg(vq + i) : T(0);
         }
-        double al = 0.0, be = 0.0, ga = 0.0;
+        T al = 0, be = 0, ga = 0;
 #pragma unroll
         for (int e = 0; e < MAXE; ++e) {
           al = fma(x[e], x[e], al);
@@ -491,18 +636,18 @@ __global__ void __launch_bounds__(128) jacobi_warp_kernel(double* W, double* V, 
           be += __shfl_xor_sync(0xffffffffu, be, o);
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        const double floor2 = 1e-32 * __ldcg(frob2 + b);
+        const T floor2 = (T)(1e-32 * __ldcg(frob2 + b));
         if (lane == 0) my_flops += 6.0 * m;
-        if (al > floor2 && be > floor2 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+        if (al > floor2 && be > floor2 && fabs(ga) > (T)tol * sqrt(al) * sqrt(be)) {
           if (lane == 0) my_flops += 6.0 * m + 6.0 * r;
-          const double zeta = (be - al) / (2.0 * ga);
-          double tt;
-          if (fabs(zeta) > 1e150)
-            tt = 0.5 / zeta;
+          const T zeta = (be - al) / (T(2) * ga);
+          T tt;
+          if (fabs(zeta) > (sizeof(T) == 8 ? T(1e150) : T(1e18)))
+            tt = T(0.5) / zeta;
           else
-            tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double c = 1.0 / sqrt(1.0 + tt * tt);
-          const double sn = c * tt;
+            tt = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          const T c = T(1) / sqrt(T(1) + tt * tt);
+          const T sn = c * tt;
 #pragma unroll
           for (int e = 0; e < MAXE; ++e) {
             const int i = lane + 32 * e;
@@ -553,8 +698,9 @@ __global__ void __launch_bounds__(128) jacobi_warp_kernel(double* W, double* V, 
   if (lane == 0) atomicAdd(flop_acc, my_flops);
   if (blockIdx.x == 0 && t == 0) {
     atomicAdd(sweeps_out, sweep);
-    for (int b = 0; b < batch; ++b)
-      if (!conv[b]) atomicOr(s.status, DEV_SVD_NOCONV);
+    if (report_noconv)
+      for (int b = 0; b < batch; ++b)
+        if (!conv[b]) atomicOr(s.status, DEV_SVD_NOCONV);
   }
 }
 
@@ -748,18 +894,18 @@ void launch_jacobi_t(double* W, double* V, int batch, int m, int r, int max_swee
   CTM_LAUNCHED();
 }
 
-template <int MAXE>
-void launch_jacobi_w(double* W, double* V, int batch, int m, int r, int max_sweeps, int* flags, int* conv,
-                     int* sweeps_out, double* frob2, double* facc, const Sync& sy, cudaStream_t st) {
+template <typename T, int MAXE>
+void launch_jacobi_w(T* W, T* V, int batch, int m, int r, int max_sweeps, double tol, int* flags, int* conv,
+                     int* sweeps_out, const double* frob2, double* facc, const Sync& sy, int report, cudaStream_t st) {
   const int threads = 128;
   int rp = r + (r & 1);
-  int grid = coop_grid((const void*)jacobi_warp_kernel<MAXE>, threads);
+  int grid = coop_grid((const void*)jacobi_warp_kernel<T, MAXE>, threads);
   int64_t need = ((int64_t)batch * (rp / 2) + 3) / 4;
   grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, need));
-  double tol = 2.220446049250313e-16 * std::max(m, r);
   Sync s = sy;
-  void* args[] = {&W, &V, &batch, &m, &r, &rp, &max_sweeps, &tol, &flags, &conv, &sweeps_out, &frob2, &facc, &s};
-  CTM_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_warp_kernel<MAXE>, grid, threads, args, 0, st));
+  void* args[] = {&W, &V, &batch, &m, &r, &rp, &max_sweeps, &tol, &flags, &conv, &sweeps_out, &frob2, &facc, &s,
+                  &report};
+  CTM_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_warp_kernel<T, MAXE>, grid, threads, args, 0, st));
   CTM_LAUNCHED();
 }
 
@@ -768,16 +914,17 @@ void launch_jacobi(double* W, double* V, int batch, int m, int r, int max_sweeps
   const int e = std::max(m, r);
   CTM_CHECK(e <= 128 * 16, CTM_ERR_INVALID_ARG, "Jacobi SVD: size too large");
   // warp-per-pair kernel for columns up to 384 long (12 doubles per lane and column in registers)
+  const double tol = 2.220446049250313e-16 * std::max(m, r);
   if (e <= 128) {
-    launch_jacobi_w<4>(W, V, batch, m, r, max_sweeps, flags, conv, sweeps_out, frob2, facc, sy, st);
+    launch_jacobi_w<double, 4>(W, V, batch, m, r, max_sweeps, tol, flags, conv, sweeps_out, frob2, facc, sy, 1, st);
     return;
   }
   if (e <= 256) {
-    launch_jacobi_w<8>(W, V, batch, m, r, max_sweeps, flags, conv, sweeps_out, frob2, facc, sy, st);
+    launch_jacobi_w<double, 8>(W, V, batch, m, r, max_sweeps, tol, flags, conv, sweeps_out, frob2, facc, sy, 1, st);
     return;
   }
   if (e <= 384) {
-    launch_jacobi_w<12>(W, V, batch, m, r, max_sweeps, flags, conv, sweeps_out, frob2, facc, sy, st);
+    launch_jacobi_w<double, 12>(W, V, batch, m, r, max_sweeps, tol, flags, conv, sweeps_out, frob2, facc, sy, 1, st);
     return;
   }
   if (e <= 256) launch_jacobi_t<2>(W, V, batch, m, r, max_sweeps, flags, conv, sweeps_out, frob2, facc, sy, st);
@@ -789,16 +936,46 @@ void launch_jacobi(double* W, double* V, int batch, int m, int r, int max_sweeps
 
 }  // namespace
 
+namespace {
+template <int MAXE>
+void launch_qr_r(double* A, double* tau, int batch, int m, int n, int64_t strideA, const Sync& sy, cudaStream_t st) {
+  const int threads = 256;
+  int grid = coop_grid((const void*)qr_kernel_r<MAXE>, threads);
+  int64_t need = ((int64_t)batch * n + threads / 32 - 1) / (threads / 32);
+  grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, need));
+  Sync s = sy;
+  void* args[] = {&A, &tau, &batch, &m, &n, &strideA, &s};
+  CTM_CUDA(cudaLaunchCooperativeKernel((const void*)qr_kernel_r<MAXE>, grid, threads, args, 0, st));
+  CTM_LAUNCHED();
+}
+
+template <int MAXE>
+void launch_apply_q_r(const double* A, const double* tau, double* X, int batch, int m, int n, int k, int64_t strideA,
+                      int64_t strideX, cudaStream_t st) {
+  const int threads = 128;
+  const int64_t need = ((int64_t)batch * k + threads / 32 - 1) / (threads / 32);
+  apply_q_cols_kernel_r<MAXE><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(need, 65535)), threads, 0, st>>>(
+      A, tau, X, batch, m, n, k, strideA, strideX);
+  CTM_LAUNCHED();
+}
+}  // namespace
+
 void qr_householder(double* A, double* tau, int batch, int m, int n, int64_t strideA, int* status, cudaStream_t st) {
   if (batch == 0 || n == 0) return;
   ProfScope ps(PROF_QR, st, batch * (2.0 * m * n * n - 2.0 * n * n * n / 3.0), 8.0 * batch * m * n * 2,
                prof_tag("qr", batch, m, n, 0));
   CoopScratch& g_coop = ensure_coop(batch, st);
+  Sync s{g_coop.bar, g_coop.abort, status, (long long)lim_spins()};
+  // columns of up to 768 rows stay in registers (4 .. 24 doubles per lane)
+  if (m <= 128) return launch_qr_r<4>(A, tau, batch, m, n, strideA, s, st);
+  if (m <= 256) return launch_qr_r<8>(A, tau, batch, m, n, strideA, s, st);
+  if (m <= 384) return launch_qr_r<12>(A, tau, batch, m, n, strideA, s, st);
+  if (m <= 512) return launch_qr_r<16>(A, tau, batch, m, n, strideA, s, st);
+  if (m <= 768) return launch_qr_r<24>(A, tau, batch, m, n, strideA, s, st);
   const int threads = 256;
   int grid = coop_grid((const void*)qr_kernel, threads);
   int64_t need = ((int64_t)batch * n + threads / 32 - 1) / (threads / 32);
   grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, need));
-  Sync s{g_coop.bar, g_coop.abort, status, (long long)lim_spins()};
   void* args[] = {&A, &tau, &batch, &m, &n, &strideA, &s};
   CTM_CUDA(cudaLaunchCooperativeKernel((const void*)qr_kernel, grid, threads, args, 0, st));
   CTM_LAUNCHED();
@@ -816,6 +993,11 @@ void qr_apply_Q(const double* A, const double* tau, double* X, int batch, int m,
   ProfScope ps(PROF_QR, st, batch * 4.0 * m * n * k - 2.0 * batch * n * n * k, 8.0 * batch * (m * n + 2.0 * m * k),
                prof_tag("apply_q", batch, m, n, k));
   (void)status;
+  if (m <= 128) return launch_apply_q_r<4>(A, tau, X, batch, m, n, k, strideA, strideX, st);
+  if (m <= 256) return launch_apply_q_r<8>(A, tau, X, batch, m, n, k, strideA, strideX, st);
+  if (m <= 384) return launch_apply_q_r<12>(A, tau, X, batch, m, n, k, strideA, strideX, st);
+  if (m <= 512) return launch_apply_q_r<16>(A, tau, X, batch, m, n, k, strideA, strideX, st);
+  if (m <= 768) return launch_apply_q_r<24>(A, tau, X, batch, m, n, k, strideA, strideX, st);
   const int threads = 128;
   const int64_t need = ((int64_t)batch * k + threads / 32 - 1) / (threads / 32);
   apply_q_cols_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(need, 65535)), threads, 0, st>>>(
@@ -1024,15 +1206,66 @@ void svd_product_full(const double* const* N, const double* const* S, const int*
   qr_extract_R(Xc, Rx, batch, nr, r, Lr, st);
   qr_householder(Rx, tau2, batch, r, r, rr, status, st);
   qr_extract_R(Rx, R2, batch, r, r, rr, st);
-  set_identity_colmajor(Vw, batch, r, st);
   CoopScratch& g_coop = ensure_coop(batch, st);
-  CTM_CUDA(cudaMemsetAsync(g_coop.flags, 0, 3 * batch * sizeof(int), st));
-  CTM_CUDA(cudaMemsetAsync(g_coop.conv, 0, batch * sizeof(int), st));
   frob2_kernel<<<batch, 256, 0, st>>>(R2, rr, g_coop.frob2);
   CTM_LAUNCHED();
   Sync sy{g_coop.bar, g_coop.abort, status, (long long)lim_spins()};
   {
     ProfScope ps(PROF_SVD, st, 0.0, 8.0 * batch * rr * 4, prof_tag("jacobi_full", batch, r, r, 0));
+    if (r <= 384) {
+      // FP32 sweeps first (GB300 runs FP32 at 64x its FP64 rate): one-sided Jacobi on an FP32 copy
+      // scaled to unit norm until the pairs are orthogonal to 1e-5, accumulating V32.  V32 is made
+      // orthogonal in FP64 by two Newton-Schulz steps V <- V (3I - V^t V)/2 (orthogonality error
+      // e -> ~e^2), the FP64 matrix is rotated by it, W <- W V, and the FP64 sweeps finish from
+      // there: near convergence one-sided Jacobi converges quadratically, so two to three FP64
+      // sweeps remain.  The result is the FP64 Jacobi SVD of R_2^t; only its starting rotation
+      // came from FP32.  Scratch: Ul (FP32 W and V), Uo, Wt (Newton-Schulz), free until finalize.
+      float* W32 = reinterpret_cast<float*>(Ul);
+      float* V32 = W32 + batch * rr;
+      double* ones = Wt;                 // unit Frobenius norms of the FP32 copies
+      double* facc32 = Wt + batch;       // the FP32 sweeps' operations (not FP64 work: not reported)
+      fill_kernel<<<1, 256, 0, st>>>(ones, batch + 1, 1.0);
+      CTM_LAUNCHED();
+      dim3 cg((unsigned)std::min<int64_t>(1024, (rr + 255) / 256), batch);
+      to_f32_unit_kernel<<<cg, 256, 0, st>>>(R2, W32, V32, r, g_coop.frob2);
+      CTM_LAUNCHED();
+      CTM_CUDA(cudaMemsetAsync(g_coop.flags, 0, 3 * batch * sizeof(int), st));
+      CTM_CUDA(cudaMemsetAsync(g_coop.conv, 0, batch * sizeof(int), st));
+      if (r <= 128)
+        launch_jacobi_w<float, 4>(W32, V32, batch, r, r, 30, 1e-5, g_coop.flags, g_coop.conv, sweeps_out, ones,
+                                  facc32, sy, 0, st);
+      else if (r <= 256)
+        launch_jacobi_w<float, 8>(W32, V32, batch, r, r, 30, 1e-5, g_coop.flags, g_coop.conv, sweeps_out, ones,
+                                  facc32, sy, 0, st);
+      else
+        launch_jacobi_w<float, 12>(W32, V32, batch, r, r, 30, 1e-5, g_coop.flags, g_coop.conv, sweeps_out, ones,
+                                   facc32, sy, 0, st);
+      f32_to_f64_kernel<<<(unsigned)std::min<int64_t>(4096, (batch * rr + 255) / 256), 256, 0, st>>>(V32, Vw,
+                                                                                                      batch * rr);
+      CTM_LAUNCHED();
+      // Row-major views of the column-major arrays: Vs = V^t, Ws = W^t.  G = V^t V = Vs Vs^t;
+      // V (3I - G)/2 has row-major view 1.5 Vs - 0.5 G Vs; W V has row-major view Vs Ws.
+      GemmSpec gg;
+      gg.M = r; gg.N = r; gg.K = r; gg.batch = batch; gg.lda = r; gg.ldb = r; gg.ldc = r;
+      gg.strideA = rr; gg.strideB = rr; gg.strideC = rr;
+      for (int it = 0; it < 2; ++it) {
+        GemmSpec g1 = gg;
+        g1.transB = true;
+        gemm_f64(Vw, Vw, Uo, g1, st);  // G = Vs Vs^t
+        CTM_CUDA(cudaMemcpyAsync(Wt, Vw, sizeof(double) * batch * rr, cudaMemcpyDeviceToDevice, st));
+        GemmSpec g2 = gg;
+        g2.alpha = -0.5;
+        g2.beta = 1.5;
+        gemm_f64(Uo, Vw, Wt, g2, st);  // 1.5 Vs - 0.5 G Vs
+        CTM_CUDA(cudaMemcpyAsync(Vw, Wt, sizeof(double) * batch * rr, cudaMemcpyDeviceToDevice, st));
+      }
+      gemm_f64(Vw, R2, Ul, gg, st);  // Ws <- Vs Ws
+      CTM_CUDA(cudaMemcpyAsync(R2, Ul, sizeof(double) * batch * rr, cudaMemcpyDeviceToDevice, st));
+    } else {
+      set_identity_colmajor(Vw, batch, r, st);
+    }
+    CTM_CUDA(cudaMemsetAsync(g_coop.flags, 0, 3 * batch * sizeof(int), st));
+    CTM_CUDA(cudaMemsetAsync(g_coop.conv, 0, batch * sizeof(int), st));
     launch_jacobi(R2, Vw, batch, r, r, lim_sweeps(), g_coop.flags, g_coop.conv, sweeps_out, g_coop.frob2,
                   g_coop.flop_acc, sy, st);
   }

@@ -16,6 +16,8 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <set>
+#include <utility>
 #include <vector>
 
 #include "kernels.h"
@@ -247,6 +249,77 @@ __global__ void qr_kernel_r(double* A, double* tau, int batch, int m, int n, int
   }
 }
 
+// Householder QR in panels of QR_PB columns.  Per panel: one block per matrix factors the panel (a
+// warp per panel column, each reflector shared through shared memory, __syncthreads between
+// reflectors), a grid barrier, then every warp applies the panel's reflectors to one trailing
+// column (held in registers), and another grid barrier: 2 grid barriers per panel instead of one
+// per column.  Each column sees the same reflectors in the same order with the same arithmetic as
+// in qr_kernel_r, so the factors are identical.  Blocks of 32 * QR_PB threads.
+constexpr int QR_PB = 8;
+
+template <int MAXE>
+__global__ void qr_panel_kernel(double* A, double* tau, int batch, int m, int n, int64_t strideA, Sync s) {
+  __shared__ double sv[QR_PB][32 * MAXE];
+  __shared__ double stau[QR_PB];
+  const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+  const int64_t gw = (int64_t)blockIdx.x * QR_PB + wid;
+  const int64_t nw = (int64_t)gridDim.x * QR_PB;
+  for (int c0 = 0; c0 < n; c0 += QR_PB) {
+    const int nb = min(QR_PB, n - c0);
+    // phase A: factor the panel
+    for (int b = blockIdx.x; b < batch; b += gridDim.x) {
+      double* Ab = A + (int64_t)b * strideA;
+      double x[MAXE];
+      if (wid < nb) load_col_r<MAXE>(Ab + (int64_t)(c0 + wid) * m, m, lane, x);
+      for (int jj = 0; jj < nb; ++jj) {
+        if (wid == jj) {
+          const double tj = make_reflector_r<MAXE>(x, c0 + jj, lane);
+#pragma unroll
+          for (int e = 0; e < MAXE; ++e) sv[jj][lane + 32 * e] = x[e];
+          if (lane == 0) stau[jj] = tj;
+        }
+        __syncthreads();
+        if (wid > jj && wid < nb) {
+          const double tj = stau[jj];
+          if (tj != 0.0) {
+            double v[MAXE];
+#pragma unroll
+            for (int e = 0; e < MAXE; ++e) v[e] = sv[jj][lane + 32 * e];
+            reflect_r<MAXE>(x, v, tj, c0 + jj, lane);
+          }
+        }
+      }
+      if (wid < nb) {
+        store_col_r<MAXE>(Ab + (int64_t)(c0 + wid) * m, m, lane, x);
+        if (lane == 0) tau[(int64_t)b * n + c0 + wid] = stau[wid];
+      }
+      __syncthreads();
+    }
+    if (!grid_barrier(s)) return;
+    // phase B: the panel's reflectors on every trailing column
+    const int64_t ncols = n - c0 - nb;
+    if (ncols > 0) {
+      const int64_t tasks = (int64_t)batch * ncols;
+      for (int64_t t = gw; t < tasks; t += nw) {
+        const int64_t b = t / ncols;
+        const int c = c0 + nb + (int)(t % ncols);
+        double* Ab = A + b * strideA;
+        double x[MAXE];
+        load_col_r<MAXE>(Ab + (int64_t)c * m, m, lane, x);
+        for (int jj = 0; jj < nb; ++jj) {
+          const double tj = __ldcg(tau + b * n + c0 + jj);
+          if (tj == 0.0) continue;
+          double v[MAXE];
+          load_col_r<MAXE>(Ab + (int64_t)(c0 + jj) * m, m, lane, v);
+          reflect_r<MAXE>(x, v, tj, c0 + jj, lane);
+        }
+        store_col_r<MAXE>(Ab + (int64_t)c * m, m, lane, x);
+      }
+      if (!grid_barrier(s)) return;
+    }
+  }
+}
+
 // X := Q X with the column of X in registers through all n reflectors.
 template <int MAXE>
 __global__ void apply_q_cols_kernel_r(const double* A, const double* tau, double* X, int batch, int m, int n, int k,
@@ -310,6 +383,168 @@ __device__ __forceinline__ void rr_pair(int round, int k, int rp, int& p, int& q
   } else {
     p = (round + k) % n1;
     q = (round - k + n1) % n1;
+  }
+}
+
+// Group of position p in round k of the circle-method tournament of G groups (position 0 fixed).
+__device__ __forceinline__ int circle_group(int k, int p, int G) { return p == 0 ? 0 : 1 + ((p - 1 - k) % (G - 1) + (G - 1)) % (G - 1); }
+
+// One-sided Jacobi in a block-cyclic order.  The columns form G groups of 4; a sweep is G - 1 outer
+// rounds in which every block holds a pair of groups (a, b) of one matrix -- its 8 columns of W and
+// V staged in shared memory -- and rotates the 16 cross pairs (a_i, b_j) in 4 inner rounds of 4
+// disjoint pairs (a warp each, separated by __syncthreads); the first outer round also rotates the
+// 12 pairs inside a and b.  Every column pair is rotated once per sweep, as in the cyclic order,
+// but only G - 1 grid barriers separate the outer rounds instead of r - 1.  Requires m = r and
+// r <= 32 * MAXE.  Convergence bookkeeping as in jacobi_warp_kernel.
+template <typename T, int MAXE>
+__global__ void __launch_bounds__(128) jacobi_block_kernel(T* W, T* V, int batch, int r, int G, int max_sweeps,
+                                                            double tol, int* flags, int* conv, int* sweeps_out,
+                                                            const double* frob2, double* flop_acc, Sync s,
+                                                            int report_noconv) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sW = reinterpret_cast<T*>(smem_raw);  // [8][r]
+  T* sV = sW + 8 * r;                      // [8][r]
+  const int t = threadIdx.x, lane = t % 32, wid = t / 32;
+  const int half = G / 2;
+  const int64_t tasks = (int64_t)batch * half;
+  const int64_t rr = (int64_t)r * r;
+  double my_flops = 0.0;
+  int sweep = 0;
+  __shared__ int any_rot;
+  for (; sweep < max_sweeps; ++sweep) {
+    int* fl = flags + (sweep % 3) * batch;
+    if (blockIdx.x == 0) {
+      int* nxt = flags + ((sweep + 1) % 3) * batch;
+      for (int b = t; b < batch; b += blockDim.x) nxt[b] = 0;
+      __threadfence();
+    }
+    for (int k = 0; k < G - 1; ++k) {
+      for (int64_t task = blockIdx.x; task < tasks; task += gridDim.x) {
+        const int b = (int)(task / half);
+        const int j = (int)(task % half);
+        if (__ldcg(conv + b)) continue;  // uniform over the block
+        const int ga = circle_group(k, j, G), gb = circle_group(k, G - 1 - j, G);
+        T* Wb = W + b * rr;
+        T* Vb = V + b * rr;
+        // stage the 8 columns: a_0..a_3 in slots 0..3, b_0..b_3 in slots 4..7 (two per warp)
+        for (int c = wid; c < 8; c += 4) {
+          const int col = (c < 4 ? ga * 4 + c : gb * 4 + c - 4);
+          for (int i = lane; i < r; i += 32) {
+            sW[c * r + i] = col < r ? __ldcg(Wb + (int64_t)col * r + i) : T(0);
+            sV[c * r + i] = col < r ? __ldcg(Vb + (int64_t)col * r + i) : T(0);
+          }
+        }
+        if (t == 0) any_rot = 0;
+        __syncthreads();
+        const T floor2 = (T)(1e-32 * __ldcg(frob2 + b));
+        const int n_inner = (k == 0) ? 7 : 4;
+        for (int it = 0; it < n_inner; ++it) {
+          int p, q;
+          if (k == 0 && it < 3) {  // pairs inside a (warps 0, 1) and inside b (warps 2, 3)
+            // (0,1)(2,3), then (0,2)(1,3), then (0,3)(1,2) within each group of four
+            const int base = (wid < 2) ? 0 : 4, w2 = wid % 2;
+            p = base + (it == 0 ? 2 * w2 : w2);
+            q = base + (it == 0 ? 2 * w2 + 1 : (it == 1 ? w2 + 2 : 3 - w2));
+          } else {
+            const int tt = (k == 0) ? it - 3 : it;
+            p = wid;
+            q = 4 + (wid + tt) % 4;
+          }
+          T x[MAXE], y[MAXE], u[MAXE], w[MAXE];
+#pragma unroll
+          for (int e = 0; e < MAXE; ++e) {
+            const int i = lane + 32 * e;
+            x[e] = i < r ? sW[p * r + i] : T(0);
+            y[e] = i < r ? sW[q * r + i] : T(0);
+            u[e] = i < r ? sV[p * r + i] : T(0);
+            w[e] = i < r ? sV[q * r + i] : T(0);
+          }
+          T al = 0, be = 0, ga_ = 0;
+#pragma unroll
+          for (int e = 0; e < MAXE; ++e) {
+            al = fma(x[e], x[e], al);
+            be = fma(y[e], y[e], be);
+            ga_ = fma(x[e], y[e], ga_);
+          }
+          for (int o = 16; o > 0; o >>= 1) {
+            al += __shfl_xor_sync(0xffffffffu, al, o);
+            be += __shfl_xor_sync(0xffffffffu, be, o);
+            ga_ += __shfl_xor_sync(0xffffffffu, ga_, o);
+          }
+          if (lane == 0) my_flops += 6.0 * r;
+          if (al > floor2 && be > floor2 && fabs(ga_) > (T)tol * sqrt(al) * sqrt(be)) {
+            if (lane == 0) my_flops += 12.0 * r;
+            const T zeta = (be - al) / (T(2) * ga_);
+            T tt;
+            if (fabs(zeta) > (sizeof(T) == 8 ? T(1e150) : T(1e18)))
+              tt = T(0.5) / zeta;
+            else
+              tt = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+            const T c = T(1) / sqrt(T(1) + tt * tt);
+            const T sn = c * tt;
+#pragma unroll
+            for (int e = 0; e < MAXE; ++e) {
+              const int i = lane + 32 * e;
+              if (i < r) {
+                sW[p * r + i] = c * x[e] - sn * y[e];
+                sW[q * r + i] = sn * x[e] + c * y[e];
+                sV[p * r + i] = c * u[e] - sn * w[e];
+                sV[q * r + i] = sn * u[e] + c * w[e];
+              }
+            }
+            if (lane == 0) any_rot = 1;
+          }
+          __syncthreads();
+        }
+        // write the 8 columns back
+        for (int c = wid; c < 8; c += 4) {
+          const int col = (c < 4 ? ga * 4 + c : gb * 4 + c - 4);
+          if (col < r)
+            for (int i = lane; i < r; i += 32) {
+              Wb[(int64_t)col * r + i] = sW[c * r + i];
+              Vb[(int64_t)col * r + i] = sV[c * r + i];
+            }
+        }
+        if (t == 0 && any_rot) fl[b] = 1;
+        __syncthreads();
+      }
+      if (!grid_barrier(s)) {
+        if (lane == 0) atomicAdd(flop_acc, my_flops);
+        return;
+      }
+    }
+    int all = 1;
+    {
+      volatile int* vf = fl;
+      volatile int* vc = conv;
+      for (int b = 0; b < batch; ++b)
+        if (!vc[b] && vf[b] != 0) all = 0;
+    }
+    if (!grid_barrier(s)) {
+      if (lane == 0) atomicAdd(flop_acc, my_flops);
+      return;
+    }
+    if (blockIdx.x == 0 && t == 0) {
+      volatile int* vf = fl;
+      for (int b = 0; b < batch; ++b)
+        if (vf[b] == 0) conv[b] = 1;
+      __threadfence();
+    }
+    if (!grid_barrier(s)) {
+      if (lane == 0) atomicAdd(flop_acc, my_flops);
+      return;
+    }
+    if (all) {
+      ++sweep;
+      break;
+    }
+  }
+  if (lane == 0) atomicAdd(flop_acc, my_flops);
+  if (blockIdx.x == 0 && t == 0) {
+    atomicAdd(sweeps_out, sweep);
+    if (report_noconv)
+      for (int b = 0; b < batch; ++b)
+        if (!conv[b]) atomicOr(s.status, DEV_SVD_NOCONV);
   }
 }
 
@@ -879,6 +1114,39 @@ int coop_grid(const void* kernel, int threads) {
   return sms * per_sm;
 }
 
+// Block-ordered Jacobi (m = r): G = ceil(r / 8) * 2 groups of 4 columns, batch * G / 2 blocks.
+template <typename T, int MAXE>
+void launch_jacobi_b(T* W, T* V, int batch, int r, int max_sweeps, double tol, int* flags, int* conv,
+                     int* sweeps_out, const double* frob2, double* facc, const Sync& sy, int report, cudaStream_t st) {
+  const int threads = 128;
+  const int G = ((r + 7) / 8) * 2;
+  const size_t smem = sizeof(T) * 16 * (size_t)r;
+  const void* fn = (const void*)jacobi_block_kernel<T, MAXE>;
+  int dev = 0;
+  CTM_CUDA(cudaGetDevice(&dev));
+  {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done.count({fn, dev})) {
+      CTM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+      done.insert({fn, dev});
+    }
+  }
+  int sms = 0, per_sm = 0;
+  CTM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CTM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
+  CTM_CHECK(per_sm > 0, CTM_ERR_CUDA, "cooperative kernel cannot be resident");
+  int64_t need = (int64_t)batch * (G / 2);
+  int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, need));
+  Sync s = sy;
+  int Gv = G;
+  void* args[] = {&W, &V, &batch, &r, &Gv, &max_sweeps, &tol, &flags, &conv, &sweeps_out, &frob2, &facc, &s,
+                  &report};
+  CTM_CUDA(cudaLaunchCooperativeKernel(fn, grid, threads, args, smem, st));
+  CTM_LAUNCHED();
+}
+
 template <int MAXE>
 void launch_jacobi_t(double* W, double* V, int batch, int m, int r, int max_sweeps, int* flags, int* conv,
                      int* sweeps_out, double* frob2, double* facc, const Sync& sy, cudaStream_t st) {
@@ -939,6 +1207,19 @@ void launch_jacobi(double* W, double* V, int batch, int m, int r, int max_sweeps
 namespace {
 template <int MAXE>
 void launch_qr_r(double* A, double* tau, int batch, int m, int n, int64_t strideA, const Sync& sy, cudaStream_t st) {
+  const int threads = 32 * QR_PB;
+  int grid = coop_grid((const void*)qr_panel_kernel<MAXE>, threads);
+  int64_t need = std::max<int64_t>(batch, ((int64_t)batch * n + QR_PB - 1) / QR_PB);
+  grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, need));
+  Sync s = sy;
+  void* args[] = {&A, &tau, &batch, &m, &n, &strideA, &s};
+  CTM_CUDA(cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<MAXE>, grid, threads, args, 0, st));
+  CTM_LAUNCHED();
+}
+
+// Unblocked variant (a grid barrier per column) for columns too long for the panel's shared memory.
+template <int MAXE>
+void launch_qr_col(double* A, double* tau, int batch, int m, int n, int64_t strideA, const Sync& sy, cudaStream_t st) {
   const int threads = 256;
   int grid = coop_grid((const void*)qr_kernel_r<MAXE>, threads);
   int64_t need = ((int64_t)batch * n + threads / 32 - 1) / (threads / 32);
@@ -966,12 +1247,13 @@ void qr_householder(double* A, double* tau, int batch, int m, int n, int64_t str
                prof_tag("qr", batch, m, n, 0));
   CoopScratch& g_coop = ensure_coop(batch, st);
   Sync s{g_coop.bar, g_coop.abort, status, (long long)lim_spins()};
-  // columns of up to 768 rows stay in registers (4 .. 24 doubles per lane)
+  // columns of up to 768 rows stay in registers (4 .. 24 doubles per lane); up to 512 rows the
+  // panel-blocked form
   if (m <= 128) return launch_qr_r<4>(A, tau, batch, m, n, strideA, s, st);
   if (m <= 256) return launch_qr_r<8>(A, tau, batch, m, n, strideA, s, st);
   if (m <= 384) return launch_qr_r<12>(A, tau, batch, m, n, strideA, s, st);
   if (m <= 512) return launch_qr_r<16>(A, tau, batch, m, n, strideA, s, st);
-  if (m <= 768) return launch_qr_r<24>(A, tau, batch, m, n, strideA, s, st);
+  if (m <= 768) return launch_qr_col<24>(A, tau, batch, m, n, strideA, s, st);
   const int threads = 256;
   int grid = coop_grid((const void*)qr_kernel, threads);
   int64_t need = ((int64_t)batch * n + threads / 32 - 1) / (threads / 32);
@@ -1232,13 +1514,13 @@ void svd_product_full(const double* const* N, const double* const* S, const int*
       CTM_CUDA(cudaMemsetAsync(g_coop.flags, 0, 3 * batch * sizeof(int), st));
       CTM_CUDA(cudaMemsetAsync(g_coop.conv, 0, batch * sizeof(int), st));
       if (r <= 128)
-        launch_jacobi_w<float, 4>(W32, V32, batch, r, r, 30, 1e-5, g_coop.flags, g_coop.conv, sweeps_out, ones,
+        launch_jacobi_b<float, 4>(W32, V32, batch, r, 30, 1e-5, g_coop.flags, g_coop.conv, sweeps_out, ones,
                                   facc32, sy, 0, st);
       else if (r <= 256)
-        launch_jacobi_w<float, 8>(W32, V32, batch, r, r, 30, 1e-5, g_coop.flags, g_coop.conv, sweeps_out, ones,
+        launch_jacobi_b<float, 8>(W32, V32, batch, r, 30, 1e-5, g_coop.flags, g_coop.conv, sweeps_out, ones,
                                   facc32, sy, 0, st);
       else
-        launch_jacobi_w<float, 12>(W32, V32, batch, r, r, 30, 1e-5, g_coop.flags, g_coop.conv, sweeps_out, ones,
+        launch_jacobi_b<float, 12>(W32, V32, batch, r, 30, 1e-5, g_coop.flags, g_coop.conv, sweeps_out, ones,
                                    facc32, sy, 0, st);
       f32_to_f64_kernel<<<(unsigned)std::min<int64_t>(4096, (batch * rr + 255) / 256), 256, 0, st>>>(V32, Vw,
                                                                                                       batch * rr);
@@ -1266,8 +1548,19 @@ void svd_product_full(const double* const* N, const double* const* S, const int*
     }
     CTM_CUDA(cudaMemsetAsync(g_coop.flags, 0, 3 * batch * sizeof(int), st));
     CTM_CUDA(cudaMemsetAsync(g_coop.conv, 0, batch * sizeof(int), st));
-    launch_jacobi(R2, Vw, batch, r, r, lim_sweeps(), g_coop.flags, g_coop.conv, sweeps_out, g_coop.frob2,
-                  g_coop.flop_acc, sy, st);
+    const double tol64 = 2.220446049250313e-16 * r;
+    if (r <= 128)
+      launch_jacobi_b<double, 4>(R2, Vw, batch, r, lim_sweeps(), tol64, g_coop.flags, g_coop.conv, sweeps_out,
+                                 g_coop.frob2, g_coop.flop_acc, sy, 1, st);
+    else if (r <= 256)
+      launch_jacobi_b<double, 8>(R2, Vw, batch, r, lim_sweeps(), tol64, g_coop.flags, g_coop.conv, sweeps_out,
+                                 g_coop.frob2, g_coop.flop_acc, sy, 1, st);
+    else if (r <= 384)
+      launch_jacobi_b<double, 12>(R2, Vw, batch, r, lim_sweeps(), tol64, g_coop.flags, g_coop.conv, sweeps_out,
+                                  g_coop.frob2, g_coop.flop_acc, sy, 1, st);
+    else
+      launch_jacobi(R2, Vw, batch, r, r, lim_sweeps(), g_coop.flags, g_coop.conv, sweeps_out, g_coop.frob2,
+                    g_coop.flop_acc, sy, st);
   }
   size_t smem = (size_t)r * (sizeof(double) + sizeof(int));
   if (smem > 48 * 1024)

@@ -249,77 +249,6 @@ __global__ void qr_kernel_r(double* A, double* tau, int batch, int m, int n, int
   }
 }
 
-// Householder QR in panels of QR_PB columns.  Per panel: one block per matrix factors the panel (a
-// warp per panel column, each reflector shared through shared memory, __syncthreads between
-// reflectors), a grid barrier, then every warp applies the panel's reflectors to one trailing
-// column (held in registers), and another grid barrier: 2 grid barriers per panel instead of one
-// per column.  Each column sees the same reflectors in the same order with the same arithmetic as
-// in qr_kernel_r, so the factors are identical.  Blocks of 32 * QR_PB threads.
-constexpr int QR_PB = 8;
-
-template <int MAXE>
-__global__ void qr_panel_kernel(double* A, double* tau, int batch, int m, int n, int64_t strideA, Sync s) {
-  __shared__ double sv[QR_PB][32 * MAXE];
-  __shared__ double stau[QR_PB];
-  const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
-  const int64_t gw = (int64_t)blockIdx.x * QR_PB + wid;
-  const int64_t nw = (int64_t)gridDim.x * QR_PB;
-  for (int c0 = 0; c0 < n; c0 += QR_PB) {
-    const int nb = min(QR_PB, n - c0);
-    // phase A: factor the panel
-    for (int b = blockIdx.x; b < batch; b += gridDim.x) {
-      double* Ab = A + (int64_t)b * strideA;
-      double x[MAXE];
-      if (wid < nb) load_col_r<MAXE>(Ab + (int64_t)(c0 + wid) * m, m, lane, x);
-      for (int jj = 0; jj < nb; ++jj) {
-        if (wid == jj) {
-          const double tj = make_reflector_r<MAXE>(x, c0 + jj, lane);
-#pragma unroll
-          for (int e = 0; e < MAXE; ++e) sv[jj][lane + 32 * e] = x[e];
-          if (lane == 0) stau[jj] = tj;
-        }
-        __syncthreads();
-        if (wid > jj && wid < nb) {
-          const double tj = stau[jj];
-          if (tj != 0.0) {
-            double v[MAXE];
-#pragma unroll
-            for (int e = 0; e < MAXE; ++e) v[e] = sv[jj][lane + 32 * e];
-            reflect_r<MAXE>(x, v, tj, c0 + jj, lane);
-          }
-        }
-      }
-      if (wid < nb) {
-        store_col_r<MAXE>(Ab + (int64_t)(c0 + wid) * m, m, lane, x);
-        if (lane == 0) tau[(int64_t)b * n + c0 + wid] = stau[wid];
-      }
-      __syncthreads();
-    }
-    if (!grid_barrier(s)) return;
-    // phase B: the panel's reflectors on every trailing column
-    const int64_t ncols = n - c0 - nb;
-    if (ncols > 0) {
-      const int64_t tasks = (int64_t)batch * ncols;
-      for (int64_t t = gw; t < tasks; t += nw) {
-        const int64_t b = t / ncols;
-        const int c = c0 + nb + (int)(t % ncols);
-        double* Ab = A + b * strideA;
-        double x[MAXE];
-        load_col_r<MAXE>(Ab + (int64_t)c * m, m, lane, x);
-        for (int jj = 0; jj < nb; ++jj) {
-          const double tj = __ldcg(tau + b * n + c0 + jj);
-          if (tj == 0.0) continue;
-          double v[MAXE];
-          load_col_r<MAXE>(Ab + (int64_t)(c0 + jj) * m, m, lane, v);
-          reflect_r<MAXE>(x, v, tj, c0 + jj, lane);
-        }
-        store_col_r<MAXE>(Ab + (int64_t)c * m, m, lane, x);
-      }
-      if (!grid_barrier(s)) return;
-    }
-  }
-}
-
 // X := Q X with the column of X in registers through all n reflectors.
 template <int MAXE>
 __global__ void apply_q_cols_kernel_r(const double* A, const double* tau, double* X, int batch, int m, int n, int k,
@@ -1207,19 +1136,6 @@ void launch_jacobi(double* W, double* V, int batch, int m, int r, int max_sweeps
 namespace {
 template <int MAXE>
 void launch_qr_r(double* A, double* tau, int batch, int m, int n, int64_t strideA, const Sync& sy, cudaStream_t st) {
-  const int threads = 32 * QR_PB;
-  int grid = coop_grid((const void*)qr_panel_kernel<MAXE>, threads);
-  int64_t need = std::max<int64_t>(batch, ((int64_t)batch * n + QR_PB - 1) / QR_PB);
-  grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, need));
-  Sync s = sy;
-  void* args[] = {&A, &tau, &batch, &m, &n, &strideA, &s};
-  CTM_CUDA(cudaLaunchCooperativeKernel((const void*)qr_panel_kernel<MAXE>, grid, threads, args, 0, st));
-  CTM_LAUNCHED();
-}
-
-// Unblocked variant (a grid barrier per column) for columns too long for the panel's shared memory.
-template <int MAXE>
-void launch_qr_col(double* A, double* tau, int batch, int m, int n, int64_t strideA, const Sync& sy, cudaStream_t st) {
   const int threads = 256;
   int grid = coop_grid((const void*)qr_kernel_r<MAXE>, threads);
   int64_t need = ((int64_t)batch * n + threads / 32 - 1) / (threads / 32);
@@ -1247,13 +1163,12 @@ void qr_householder(double* A, double* tau, int batch, int m, int n, int64_t str
                prof_tag("qr", batch, m, n, 0));
   CoopScratch& g_coop = ensure_coop(batch, st);
   Sync s{g_coop.bar, g_coop.abort, status, (long long)lim_spins()};
-  // columns of up to 768 rows stay in registers (4 .. 24 doubles per lane); up to 512 rows the
-  // panel-blocked form
+  // columns of up to 768 rows stay in registers (4 .. 24 doubles per lane)
   if (m <= 128) return launch_qr_r<4>(A, tau, batch, m, n, strideA, s, st);
   if (m <= 256) return launch_qr_r<8>(A, tau, batch, m, n, strideA, s, st);
   if (m <= 384) return launch_qr_r<12>(A, tau, batch, m, n, strideA, s, st);
   if (m <= 512) return launch_qr_r<16>(A, tau, batch, m, n, strideA, s, st);
-  if (m <= 768) return launch_qr_col<24>(A, tau, batch, m, n, strideA, s, st);
+  if (m <= 768) return launch_qr_r<24>(A, tau, batch, m, n, strideA, s, st);
   const int threads = 256;
   int grid = coop_grid((const void*)qr_kernel, threads);
   int64_t need = ((int64_t)batch * n + threads / 32 - 1) / (threads / 32);

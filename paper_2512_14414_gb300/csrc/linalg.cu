@@ -1,12 +1,14 @@
-// FP64 dense linear algebra of the projector step: batched Householder QR
-// (Golub & Van Loan, Alg. 5.2.1 with LAPACK's reflector convention) and
-// batched one-sided Jacobi SVD (Hestenes 1958; Rutishauser's rotation,
-// cyclic round-robin ordering as in Brent & Luk 1985).
+// Dense linear algebra of the projector step: batched Householder QR (FP64;
+// Golub & Van Loan, Alg. 5.2.1 with LAPACK's reflector convention) and batched
+// one-sided Jacobi SVD (Hestenes 1958; Rutishauser's rotation; cyclic
+// round-robin ordering as in Brent & Luk 1985, or a block-cyclic ordering of
+// groups of four columns), with an optional FP32 pre-pass before the FP64
+// sweeps (see svd_product_full).
 //
 // Columns move between blocks from one step to the next, so every load of
 // shared state in these kernels bypasses L1 (ld.global.cg).
 //
-// All three sweep-style kernels are persistent cooperative launches whose
+// The QR and Jacobi kernels are persistent cooperative launches whose
 // blocks meet at a software grid barrier between dependent steps.  Every
 // wait is bounded: a block that waits too long raises DEV_TIMEOUT in the
 // status word, sets the shared abort flag and returns; the others see the
@@ -492,114 +494,11 @@ __global__ void frob2_kernel(const double* W, int64_t rr, double* out) {
   if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
 }
 
-// A pair is rotated when |g| > tol sqrt(a) sqrt(b) (products of square roots cannot underflow) and
-// both columns lie above the rounding floor 1e-32 ||M||_F^2: below it a column is noise whose
-// direction no further rotation can settle, and its singular value is a numerical zero.
-__global__ void jacobi_kernel(double* W, double* V, int batch, int r, int rp, int max_sweeps, double tol, int* flags,
-                              int* conv, int* sweeps_out, const double* frob2, double* flop_acc, Sync s) {
-  const int lane = threadIdx.x % 32;
-  double my_flops = 0.0;  // 6r per pair test, 12r per rotation (both columns of W and V)
-  const int wpb = blockDim.x / 32;
-  const int64_t gw = (int64_t)blockIdx.x * wpb + threadIdx.x / 32;
-  const int64_t nw = (int64_t)gridDim.x * wpb;
-  const int npairs = rp / 2;
-  const int64_t tasks = (int64_t)batch * npairs;
-  const int64_t rr = (int64_t)r * r;
-  int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
-    int* fl = flags + (sweep % 3) * batch;
-    if (blockIdx.x == 0) {
-      int* nxt = flags + ((sweep + 1) % 3) * batch;
-      for (int b = threadIdx.x; b < batch; b += blockDim.x) nxt[b] = 0;
-      __threadfence();
-    }
-    for (int round = 0; round < rp - 1; ++round) {
-      for (int64_t t = gw; t < tasks; t += nw) {
-        const int b = (int)(t / npairs);
-        if (__ldcg(conv + b)) continue;
-        int p, q;
-        rr_pair(round, (int)(t % npairs), rp, p, q);
-        if (p >= r || q >= r) continue;
-        double* ap = W + b * rr + (int64_t)p * r;
-        double* aq = W + b * rr + (int64_t)q * r;
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int i = lane; i < r; i += 32) {
-          double x = __ldcg(ap + i), y = __ldcg(aq + i);
-          al = fma(x, x, al);
-          be = fma(y, y, be);
-          ga = fma(x, y, ga);
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        const double floor2 = 1e-32 * __ldcg(frob2 + b);
-        my_flops += 6.0 * r;
-        if (al > floor2 && be > floor2 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-          my_flops += 12.0 * r;
-          double zeta = (be - al) / (2.0 * ga);
-          double tt;
-          if (fabs(zeta) > 1e150)
-            tt = 0.5 / zeta;
-          else
-            tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          double c = 1.0 / sqrt(1.0 + tt * tt);
-          double sn = c * tt;
-          for (int i = lane; i < r; i += 32) {
-            double x = __ldcg(ap + i), y = __ldcg(aq + i);
-            ap[i] = c * x - sn * y;
-            aq[i] = sn * x + c * y;
-          }
-          double* vp = V + b * rr + (int64_t)p * r;
-          double* vq = V + b * rr + (int64_t)q * r;
-          for (int i = lane; i < r; i += 32) {
-            double x = __ldcg(vp + i), y = __ldcg(vq + i);
-            vp[i] = c * x - sn * y;
-            vq[i] = sn * x + c * y;
-          }
-          if (lane == 0) fl[b] = 1;
-        }
-        __syncwarp();
-      }
-      if (!grid_barrier(s)) {
-        if (lane == 0) atomicAdd(flop_acc, my_flops);
-        return;
-      }
-    }
-    // decide convergence: every block reads the same flags and conv after the barrier
-    int all = 1;
-    {
-      volatile int* vf = fl;
-      volatile int* vc = conv;
-      for (int b = 0; b < batch; ++b)
-        if (!vc[b] && vf[b] != 0) all = 0;
-    }
-    if (!grid_barrier(s)) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      volatile int* vf = fl;
-      for (int b = 0; b < batch; ++b)
-        if (vf[b] == 0) conv[b] = 1;
-      __threadfence();
-    }
-    if (!grid_barrier(s)) return;
-    if (all) {
-      ++sweep;
-      break;
-    }
-  }
-  if (lane == 0) atomicAdd(flop_acc, my_flops);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    atomicAdd(sweeps_out, sweep);
-    for (int b = 0; b < batch; ++b)
-      if (!conv[b]) atomicOr(s.status, DEV_SVD_NOCONV);
-  }
-}
-
-// Same sweeps with one 128-thread block per column pair: every thread holds MAXE rows of the
-// two columns of W and of V in registers (loads issued together), the three dot products are
-// reduced across the block, and the rotation is applied in registers before the stores.
-// Requires r <= 128 * MAXE.
-// W holds n columns of length m per matrix (column-major, stride m*n), V n columns of length n.
-// Same sweeps with one 128-thread block per column pair: every thread holds MAXE rows of the
+// Cyclic one-sided Jacobi sweeps (round-robin pairing, a grid barrier per round).  A pair is rotated
+// when |g| > tol sqrt(a) sqrt(b) (products of square roots cannot underflow) and both columns lie
+// above the rounding floor 1e-32 ||M||_F^2: below it a column is noise whose direction no further
+// rotation can settle, and its singular value is a numerical zero.
+// One 128-thread block per column pair: every thread holds MAXE rows of the
 // two columns of W and of V in registers (loads issued together), the three dot products are
 // reduced across the block, and the rotation is applied in registers before the stores.
 // Requires max(m, r) <= 128 * MAXE.  The rotation test and the rotation itself (square roots and

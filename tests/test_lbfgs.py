@@ -55,3 +55,54 @@ def test_lowers_the_oracle_energy_of_a_small_peps():
     assert res.n_iter >= 1
     assert res.history[-1] < res.history[0] - 1e-4
     assert all(b <= a + 1e-12 for a, b in zip(res.history, res.history[1:]))
+
+
+class _FakeCTM:
+    """Stands in for the GPU handle: an 'environment' that relaxes towards a function of A by a
+    factor 10 per iteration, and a quadratic energy whose gradient grad_fixed_point returns."""
+
+    def __init__(self, target):
+        import torch
+        self.torch, self.target = torch, target
+        self.inits, self.steps = [], 0
+
+    def init(self, A, env):
+        self.A, self.env = A.clone(), env.clone()
+        self.inits.append(env.clone())
+
+    def step(self, n):
+        goal = self.A.flatten()[: self.env.numel()] + 1.0
+        delta = 0.0
+        for _ in range(n):
+            new = goal + 0.1 * (self.env - goal)
+            delta = float((new - self.env).abs().max())
+            self.env = new
+            self.steps += 1
+        return delta
+
+    def get_env(self):
+        return self.env.clone()
+
+    def grad_fixed_point(self, tol=1e-10):
+        d = self.A - self.target
+        return self.torch.tensor([float((d * d).sum())]), 2 * d, 7, 0.0
+
+
+def test_fixed_point_driver_warm_starts_and_converges_each_evaluation():
+    # optimize_peps(gradient="fixed_point"): every evaluation starts from the environment the previous
+    # one converged, iterates until the spectrum change is below conv_tol, then takes the fixed-point
+    # gradient; L-BFGS drives the quadratic to its minimum
+    import torch
+    from paper_2512_14414_gb300.lbfgs import optimize_peps
+    target = torch.arange(6, dtype=torch.float64).reshape(1, 6) / 7.0
+    ctm = _FakeCTM(target)
+    env0 = torch.zeros(3, dtype=torch.float64)
+    res = optimize_peps(ctm, np.zeros((1, 6)), env0, n_iter=50, max_steps=20, gradient="fixed_point",
+                        conv_tol=1e-9)
+    assert np.allclose(res.x, target.numpy().ravel(), atol=1e-6)
+    assert torch.equal(ctm.inits[0], env0)
+    assert len(ctm.inits) == res.n_eval >= 2
+    # each later evaluation starts where the previous one ended (not from env0)
+    assert not torch.equal(ctm.inits[1], env0)
+    # iterations come in chunks of 5 until the change is below 1e-9 (10x contraction: 10 iterations)
+    assert ctm.steps % 5 == 0 and ctm.steps >= 10 * res.n_eval

@@ -504,3 +504,41 @@ def test_fixed_point_gradient_is_the_limit_of_the_unrolled_one(_converged_d2):
         errs.append(np.linalg.norm(gu[0] - g[0]) / np.linalg.norm(g[0]))
     assert errs[1] <= 1e-7 and errs[1] < errs[0] / 100, errs
     assert abs(np.sum(g[0] * w.tensors[0])) <= 1e-10 * np.linalg.norm(g[0]) * np.linalg.norm(w.tensors[0])
+
+
+# ----------------------------------------------------------------------------- warm-start network
+def test_mlp_gradient_matches_central_differences_of_the_loss():
+    from oracle import mlp
+    rng = np.random.default_rng(5)
+    dims = [7, 6, 5, 4]
+    W = [rng.standard_normal((dims[k + 1], dims[k])) / 2 for k in range(3)]
+    b = [rng.standard_normal(dims[k + 1]) / 2 for k in range(3)]
+    x = rng.standard_normal((3, 7))
+    t = rng.standard_normal((3, 4))
+    L, dW, db = mlp.loss_and_grad(x, t, W, b)
+    h = 1e-6
+    for k in range(3):
+        for (i, j) in ((0, 0), (dims[k + 1] - 1, dims[k] - 1), (1, 2)):
+            Wp = [w.copy() for w in W]
+            Wm = [w.copy() for w in W]
+            Wp[k][i, j] += h
+            Wm[k][i, j] -= h
+            fd = (mlp.loss_and_grad(x, t, Wp, b)[0] - mlp.loss_and_grad(x, t, Wm, b)[0]) / (2 * h)
+            assert abs(dW[k][i, j] - fd) <= 1e-8 * max(1.0, abs(fd)), (k, i, j)
+        bp = [v.copy() for v in b]
+        bm = [v.copy() for v in b]
+        bp[k][1] += h
+        bm[k][1] -= h
+        fd = (mlp.loss_and_grad(x, t, W, bp)[0] - mlp.loss_and_grad(x, t, W, bm)[0]) / (2 * h)
+        assert abs(db[k][1] - fd) <= 1e-8 * max(1.0, abs(fd))
+
+
+def test_gelu_derivative_and_adam_first_step():
+    from oracle import mlp
+    z = np.linspace(-4, 4, 17)
+    h = 1e-6
+    assert np.allclose(mlp.gelu_prime(z), (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h), atol=1e-9)
+    assert np.allclose(mlp.gelu(np.array([0.0, 10.0, -10.0])), [0.0, 10.0, 0.0], atol=1e-12)
+    g = np.array([0.3, -2.0, 1e-3])
+    p, m, v = mlp.adam_step(np.zeros(3), g, np.zeros(3), np.zeros(3), 0.01, 0.9, 0.999, 1e-8, 1)
+    assert np.allclose(p, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)

@@ -264,6 +264,35 @@ int ctm_get_spectra(ctm_handle* h, int iter, double* out_host, int max_pairs, in
 int ctm_mlp_forward(const float* x, int batch, int n_layers, const int* dims, const float* const* W,
                     const float* const* b, float* work, float* y, void* stream);
 
+/* Work size (FP32 elements) that ctm_mlp_backward needs for this network and batch; -1 on bad
+ * arguments (same limits as ctm_mlp_forward). */
+int64_t ctm_mlp_work_floats(int batch, int n_layers, const int* dims);
+
+/* Gradient of the warm-start network's training loss, the mean-squared error
+ *     L = sum (y - target)^2 / (batch * dims[n_layers]),  y = the forward pass of ctm_mlp_forward,
+ * by the chain rule layer by layer: the forward pass is recomputed keeping each hidden layer's
+ * pre-activation z_k, then dL/dz_L = 2 (y - target) / (batch * n_out), dW_k = (dL/dz_k)^t h_k,
+ * db_k = sum over the batch of dL/dz_k, dL/dh_k = dL/dz_k W_k and
+ * dL/dz_{k-1} = dL/dh_k * GELU'(z_{k-1}) with GELU'(z) = Phi(z) + z phi(z) (exact GELU).
+ *   x, target : device, FP32, batch x dims[0] and batch x dims[n_layers] (row-major).
+ *   W, b      : as ctm_mlp_forward (b == NULL: no biases).
+ *   dW[k]     : device, FP32, the shape of W[k] (overwritten); dW is a HOST array of pointers.
+ *   db[k]     : device, FP32, dims[k+1] entries (overwritten), or db == NULL; HOST array.
+ *   work      : device, FP32, ctm_mlp_work_floats(batch, n_layers, dims) elements (caller-owned).
+ *   loss_dev  : device, 1 float receiving L, or NULL.
+ * Enqueued on the stream; no allocation.  Training is an offline step: the energy and gradient
+ * path never calls it. */
+int ctm_mlp_backward(const float* x, const float* target, int batch, int n_layers, const int* dims,
+                     const float* const* W, const float* const* b, float* const* dW, float* const* db, float* work,
+                     float* loss_dev, void* stream);
+
+/* One Adam step (Kingma & Ba 2015) on n FP32 parameters, all device arrays updated in place:
+ *   m = beta1 m + (1 - beta1) g;  v = beta2 v + (1 - beta2) g^2;
+ *   p -= lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps).
+ * t >= 1 is the step count; 0 <= beta1, beta2 < 1. */
+int ctm_adam_step(float* p, const float* g, float* m, float* v, int64_t n, float lr, float beta1, float beta2,
+                  float eps, int t, void* stream);
+
 int ctm_destroy(ctm_handle* h);
 const char* ctm_error_string(int status);
 

@@ -12,7 +12,7 @@ PRECISIONS = {"fp64": CTM_FP64, "tf32": CTM_TF32, "bf16": CTM_BF16, "tf32x3": CT
 
 EXPORTS = ["ctm_create", "ctm_init", "ctm_step", "ctm_energy", "ctm_grad", "ctm_grad_fixed_point", "ctm_get_env", "ctm_set_env",
            "ctm_env_numel", "ctm_kernel_launches", "ctm_set_limits", "ctm_magnetization", "ctm_plaquette_order", "ctm_profile", "ctm_profile_read", "ctm_svd", "ctm_svd_noalloc",
-           "ctm_get_spectra", "ctm_mlp_forward", "ctm_destroy", "ctm_error_string"]
+           "ctm_get_spectra", "ctm_mlp_forward", "ctm_mlp_work_floats", "ctm_mlp_backward", "ctm_adam_step", "ctm_destroy", "ctm_error_string"]
 PROF_CLASSES = {"gemm": 0, "permute": 1, "svd": 2, "qr": 3, "misc": 4, "tc_gemm": 5, "gemm_f64": 6}
 
 
@@ -62,6 +62,12 @@ def load():
     lib.ctm_svd_noalloc.argtypes = [vp, i, i, vp, vp, vp, vp]
     lib.ctm_get_spectra.argtypes = [vp, i, vp, i, i, ctypes.POINTER(i)]
     lib.ctm_mlp_forward.argtypes = [vp, i, i, ctypes.POINTER(i), ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, vp]
+    lib.ctm_mlp_work_floats.argtypes = [i, i, ctypes.POINTER(i)]
+    lib.ctm_mlp_work_floats.restype = i64
+    lib.ctm_mlp_backward.argtypes = [vp, vp, i, i, ctypes.POINTER(i), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                     ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, vp]
+    lib.ctm_adam_step.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                  ctypes.c_float, i, vp]
     lib.ctm_destroy.argtypes = [vp]
     lib.ctm_error_string.argtypes = [i]
     lib.ctm_error_string.restype = ctypes.c_char_p

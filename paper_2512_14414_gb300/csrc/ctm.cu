@@ -1600,6 +1600,35 @@ int ctm_mlp_forward(const float* x, int batch, int n_layers, const int* dims, co
   return guard(nullptr, [&]() { ctm::mlp_forward(x, batch, n_layers, dims, W, b, work, y, (cudaStream_t)stream); });
 }
 
+int64_t ctm_mlp_work_floats(int batch, int n_layers, const int* dims) {
+  if (!dims || batch < 1 || n_layers < 1 || n_layers > 16) return -1;
+  for (int k = 0; k <= n_layers; ++k)
+    if (dims[k] < 1) return -1;
+  return ctm::mlp_work_floats(batch, n_layers, dims);
+}
+
+int ctm_mlp_backward(const float* x, const float* target, int batch, int n_layers, const int* dims,
+                     const float* const* W, const float* const* b, float* const* dW, float* const* db, float* work,
+                     float* loss_dev, void* stream) {
+  if (!x || !target || !dims || !W || !dW || !work || batch < 1 || n_layers < 1 || n_layers > 16)
+    return CTM_ERR_INVALID_ARG;
+  for (int k = 0; k <= n_layers; ++k)
+    if (dims[k] < 1) return CTM_ERR_INVALID_ARG;
+  for (int k = 0; k < n_layers; ++k)
+    if (!W[k] || !dW[k] || (b && db && b[k] && !db[k])) return CTM_ERR_INVALID_ARG;
+  return guard(nullptr, [&]() {
+    ctm::mlp_backward(x, target, batch, n_layers, dims, W, b, dW, b ? db : nullptr, work, loss_dev,
+                      (cudaStream_t)stream);
+  });
+}
+
+int ctm_adam_step(float* p, const float* g, float* m, float* v, int64_t n, float lr, float beta1, float beta2,
+                  float eps, int t, void* stream) {
+  if (!p || !g || !m || !v || n < 1 || t < 1 || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f))
+    return CTM_ERR_INVALID_ARG;
+  return guard(nullptr, [&]() { ctm::adam_step(p, g, m, v, n, lr, beta1, beta2, eps, t, (cudaStream_t)stream); });
+}
+
 int ctm_svd(const double* M, int batch, int r, double* U, double* s, double* V, void* stream) {
   if (!M || !U || !s || !V || batch < 1 || r < 1 || r > 4096) return CTM_ERR_INVALID_ARG;
   return guard(nullptr, [&]() {

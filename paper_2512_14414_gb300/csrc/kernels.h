@@ -53,6 +53,12 @@ void gemm_tc_x3_bf16(const void* Ahi, const void* Alo, const void* Bhi, const vo
 // b[k] has dims[k+1] entries (b may be null); work holds 2 * batch * max hidden width floats.
 void mlp_forward(const float* x, int batch, int n_layers, const int* dims, const float* const* W,
                  const float* const* b, float* work, float* y, cudaStream_t st);
+int64_t mlp_work_floats(int batch, int n_layers, const int* dims);
+void mlp_backward(const float* x, const float* target, int batch, int n_layers, const int* dims,
+                  const float* const* W, const float* const* b, float* const* dW, float* const* db, float* work,
+                  float* loss, cudaStream_t st);
+void adam_step(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2, float eps, int t,
+               cudaStream_t st);
 // hi = x rounded to BF16, lo = (x - hi) rounded to BF16 (BF16 outputs).
 void split_bf16(const float* x, void* hi, void* lo, int64_t n, cudaStream_t st);
 

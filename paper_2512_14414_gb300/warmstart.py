@@ -10,8 +10,10 @@ standard initial environment, in fewer iterations when the prediction is close.
 * inference: ``ctm_mlp_forward`` (the library's GEMMs + a fused bias/GELU kernel);
 * training data: (A, converged environment) pairs harvested by running the GPU CTMRG to a
   spectrum change below ``tol`` from the standard initial environment;
-* training: plain torch (Adam on the mean-squared error of the normalised environment) -- an
-  offline step, not part of the energy/gradient path.
+* training: Adam on the mean-squared error of the normalised environment, on the GPU through the
+  library's own kernels (``ctm_mlp_backward`` for the gradient, ``ctm_adam_step`` for the update);
+  a network kept on the CPU trains with plain torch instead.  Training is an offline step, not
+  part of the energy/gradient path.
 
 The environment is gauge dependent; the projector construction (sorted singular vectors with a
 sign rule) fixes its basis well enough for a regression target, and where it does not the
@@ -48,7 +50,7 @@ def normalise_env(env: torch.Tensor, sizes: Sequence[int]) -> torch.Tensor:
 
 
 class WarmStart:
-    """The network: weights as torch tensors (trained with torch), inference through libctm."""
+    """The network: weights as torch tensors; inference and (on the GPU) training through libctm."""
 
     def __init__(self, n_in: int, n_out: int, hidden: int = HIDDEN, n_hidden: int = N_HIDDEN, seed: int = 0,
                  device: str = "cuda"):
@@ -92,17 +94,60 @@ class WarmStart:
                 h = torch.nn.functional.gelu(h)
         return h
 
+    def loss_and_grad(self, x: torch.Tensor, target: torch.Tensor):
+        """Mean-squared error and its gradient with respect to every W_k and b_k, through
+        ``ctm_mlp_backward``.  x: (batch, n_in) normalised FP32 inputs on the GPU."""
+        lib = _lib.load()
+        x = x.to(torch.float32).contiguous()
+        target = target.to(torch.float32).contiguous()
+        batch = x.shape[0]
+        n = len(self.dims) - 1
+        dims = (ctypes.c_int * (n + 1))(*self.dims)
+        nwork = lib.ctm_mlp_work_floats(batch, n, dims)
+        if nwork < 0:
+            raise ValueError("bad network shape")
+        work = torch.empty(int(nwork), dtype=torch.float32, device=x.device)
+        dW = [torch.empty_like(w) for w in self.W]
+        db = [torch.empty_like(b) for b in self.b]
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        vp = ctypes.c_void_p
+        _check(lib.ctm_mlp_backward(vp(x.data_ptr()), vp(target.data_ptr()), batch, n, dims,
+                                    (vp * n)(*[w.data_ptr() for w in self.W]), (vp * n)(*[b.data_ptr() for b in self.b]),
+                                    (vp * n)(*[g.data_ptr() for g in dW]), (vp * n)(*[g.data_ptr() for g in db]),
+                                    vp(work.data_ptr()), vp(loss.data_ptr()), _stream()), "ctm_mlp_backward")
+        return loss, dW, db
+
     def fit(self, A: torch.Tensor, Y: torch.Tensor, epochs: int = 300, lr: float = 1e-3,
             batch_size: int = 64, seed: int = 0) -> List[float]:
-        """Adam on the mean-squared error between prediction and normalised target environments."""
+        """Adam on the mean-squared error between prediction and normalised target environments
+        (beta1 0.9, beta2 0.999, eps 1e-8): libctm's kernels when the network is on the GPU."""
         x = A.reshape(A.shape[0], -1).to(torch.float32)
         self.mean = x.mean(0)
         self.scale = x.std(0).clamp_min(1e-6) if x.shape[0] > 1 else torch.ones_like(self.mean)
-        params = [t.requires_grad_(True) for t in self.W + self.b]
-        opt = torch.optim.Adam(params, lr=lr)
         g = torch.Generator(device="cpu").manual_seed(seed)
         losses = []
         n = A.shape[0]
+        if self.W[0].is_cuda:
+            lib = _lib.load()
+            params = self.W + self.b
+            moments = [(torch.zeros_like(p), torch.zeros_like(p)) for p in params]
+            step = 0
+            for _ in range(epochs):
+                perm = torch.randperm(n, generator=g)
+                tot = 0.0
+                for i in range(0, n, batch_size):
+                    idx = perm[i:i + batch_size].to(A.device)
+                    loss, dW, db = self.loss_and_grad(self._inputs(A[idx]), Y[idx])
+                    step += 1
+                    for p, gr, (m, v) in zip(params, dW + db, moments):
+                        _check(lib.ctm_adam_step(ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(gr.data_ptr()),
+                                                 ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(v.data_ptr()),
+                                                 p.numel(), lr, 0.9, 0.999, 1e-8, step, _stream()), "ctm_adam_step")
+                    tot += float(loss[0]) * len(idx)
+                losses.append(tot / n)
+            return losses
+        params = [t.requires_grad_(True) for t in self.W + self.b]
+        opt = torch.optim.Adam(params, lr=lr)
         for _ in range(epochs):
             perm = torch.randperm(n, generator=g)
             tot = 0.0

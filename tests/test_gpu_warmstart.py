@@ -1,4 +1,5 @@
-"""Learned warm start on the GPU: the MLP kernels against torch FP32, and CTMRG from a prediction."""
+"""Learned warm start on the GPU: the MLP forward against torch FP32, its backward and the Adam step
+against the FP64 oracle, training through the library's kernels, and CTMRG from a prediction."""
 import numpy as np
 import pytest
 import torch
@@ -38,3 +39,44 @@ def test_warm_started_ctmrg_reaches_the_cold_start_fixed_point():
         n1, E1, ok1 = converge(ctm, At, pred)
         assert ok0 and ok1, (n0, n1)
         assert abs(E1 - E0) <= 1e-7, (E0, E1)
+
+
+def test_mlp_backward_matches_the_oracle():
+    # loss and gradient of every W_k and b_k through ctm_mlp_backward (FP32 kernels) against the
+    # FP64 oracle's chain rule, at the network's real sizes for D=2, chi=8 (3 x 1024 hidden), batch 8
+    from oracle import mlp
+    w = W.config("heis_d2_chi8")
+    n_out = sum(env_tensor_sizes(w.Lx, w.Ly, w.D, w.d, w.chi))
+    net = WarmStart(w.d * w.D ** 4, n_out, seed=4)
+    A = torch.tensor(np.stack(ising_states(w, range(8))), device="cuda")
+    x = net._inputs(A)
+    target = torch.randn(8, n_out, generator=torch.Generator().manual_seed(9)).to("cuda")
+    loss, dW, db = net.loss_and_grad(x, target)
+    torch.cuda.synchronize()
+    L, dWr, dbr = mlp.loss_and_grad(x.cpu().numpy(), target.cpu().numpy(), [t.cpu().numpy() for t in net.W],
+                                    [t.cpu().numpy() for t in net.b])
+    assert abs(float(loss[0]) - L) <= 1e-5 * L
+    for k in range(len(dW)):
+        g, gr = dW[k].cpu().numpy(), dWr[k]
+        assert np.linalg.norm(g - gr) <= 1e-4 * np.linalg.norm(gr), k
+        g, gr = db[k].cpu().numpy(), dbr[k]
+        assert np.linalg.norm(g - gr) <= 1e-4 * np.linalg.norm(gr), k
+
+
+def test_adam_step_matches_the_oracle():
+    import ctypes
+    from oracle import mlp
+    from paper_2512_14414_gb300 import _lib
+    from paper_2512_14414_gb300.api import _check, _stream
+    rng = np.random.default_rng(11)
+    p, g, m = (rng.standard_normal(5000).astype(np.float32) for _ in range(3))
+    v = rng.random(5000).astype(np.float32)
+    dev = [torch.tensor(a, device="cuda") for a in (p, g, m, v)]
+    lib = _lib.load()
+    _check(lib.ctm_adam_step(*[ctypes.c_void_p(t.data_ptr()) for t in dev], 5000, 1e-3, 0.9, 0.999, 1e-8, 3,
+                             _stream()), "ctm_adam_step")
+    torch.cuda.synchronize()
+    pr, mr, vr = mlp.adam_step(p, g, m, v, 1e-3, 0.9, 0.999, 1e-8, 3)
+    assert np.allclose(dev[0].cpu().numpy(), pr, rtol=1e-6, atol=1e-7)
+    assert np.allclose(dev[2].cpu().numpy(), mr, rtol=1e-6, atol=1e-7)
+    assert np.allclose(dev[3].cpu().numpy(), vr, rtol=1e-6, atol=1e-7)

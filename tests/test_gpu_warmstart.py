@@ -76,7 +76,9 @@ def test_adam_step_matches_the_oracle():
     _check(lib.ctm_adam_step(*[ctypes.c_void_p(t.data_ptr()) for t in dev], 5000, 1e-3, 0.9, 0.999, 1e-8, 3,
                              _stream()), "ctm_adam_step")
     torch.cuda.synchronize()
-    pr, mr, vr = mlp.adam_step(p, g, m, v, 1e-3, 0.9, 0.999, 1e-8, 3)
+    # the hyperparameters reach the kernel as FP32 values: the oracle takes the same rounded values
+    f32 = lambda c: float(np.float32(c))
+    pr, mr, vr = mlp.adam_step(p, g, m, v, f32(1e-3), f32(0.9), f32(0.999), f32(1e-8), 3)
     assert np.allclose(dev[0].cpu().numpy(), pr, rtol=1e-6, atol=1e-7)
     assert np.allclose(dev[2].cpu().numpy(), mr, rtol=1e-6, atol=1e-7)
     assert np.allclose(dev[3].cpu().numpy(), vr, rtol=1e-6, atol=1e-7)

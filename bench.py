@@ -240,8 +240,12 @@ def run_reference(args, w):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t1, "higher_is_better": True,
         "extrapolated_eval_seconds": est,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "Lx": w.Lx, "Ly": w.Ly, "D": w.D, "chi": w.chi, "n_iter": w.n_iter,
-                   "model": "Shastry-Sutherland J=0.7 J'=1" if w.name.startswith("ss") else "Heisenberg"},
+        "config": {"workload": w.name, "model": "Shastry-Sutherland J=0.7 J'=1" if w.name.startswith("ss")
+                   else "Heisenberg (sublattice-rotated)", "Lx": w.Lx, "Ly": w.Ly, "D": w.D, "chi": w.chi,
+                   "n_iter": w.n_iter, "precision": "fp64", "parallelism": "oracle, host cores",
+                   "inputs": "noisy_ising_site: sign-free Ising core + 0.15 N(0,1) per entry, seeds 2-5",
+                   "env0": "the seeded random environment (an iteration of the oracle costs the same from "
+                           "any start)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libctm.so")
 SOURCES = ["kernels.cu", "linalg.cu", "tc_gemm.cu", "engine.cu", "ctm.cu", "mlp.cu"]
-HEADERS = ["common.h", "kernels.h", "engine.h", "stride_map.h"]
+HEADERS = ["common.h", "kernels.h", "engine.h", "stride_map.h", "jacobi_order.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-diag-suppress", "550"]

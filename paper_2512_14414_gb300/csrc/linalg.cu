@@ -22,6 +22,7 @@
 #include <utility>
 #include <vector>
 
+#include "jacobi_order.h"
 #include "kernels.h"
 
 namespace ctm {
@@ -317,9 +318,6 @@ __device__ __forceinline__ void rr_pair(int round, int k, int rp, int& p, int& q
   }
 }
 
-// Group of position p in round k of the circle-method tournament of G groups (position 0 fixed).
-__device__ __forceinline__ int circle_group(int k, int p, int G) { return p == 0 ? 0 : 1 + ((p - 1 - k) % (G - 1) + (G - 1)) % (G - 1); }
-
 // One-sided Jacobi in a block-cyclic order.  The columns form G groups of 4; a sweep is G - 1 outer
 // rounds in which every block holds a pair of groups (a, b) of one matrix -- its 8 columns of W and
 // V staged in shared memory -- and rotates the 16 cross pairs (a_i, b_j) in 4 inner rounds of 4
@@ -368,19 +366,10 @@ __global__ void __launch_bounds__(128) jacobi_block_kernel(T* W, T* V, int batch
         if (t == 0) any_rot = 0;
         __syncthreads();
         const T floor2 = (T)(1e-32 * __ldcg(frob2 + b));
-        const int n_inner = (k == 0) ? 7 : 4;
+        const int n_inner = block_inner_rounds(k);
         for (int it = 0; it < n_inner; ++it) {
           int p, q;
-          if (k == 0 && it < 3) {  // pairs inside a (warps 0, 1) and inside b (warps 2, 3)
-            // (0,1)(2,3), then (0,2)(1,3), then (0,3)(1,2) within each group of four
-            const int base = (wid < 2) ? 0 : 4, w2 = wid % 2;
-            p = base + (it == 0 ? 2 * w2 : w2);
-            q = base + (it == 0 ? 2 * w2 + 1 : (it == 1 ? w2 + 2 : 3 - w2));
-          } else {
-            const int tt = (k == 0) ? it - 3 : it;
-            p = wid;
-            q = 4 + (wid + tt) % 4;
-          }
+          block_pair(k, it, wid, p, q);  // slots of this warp's pair (jacobi_order.h)
           T x[MAXE], y[MAXE], u[MAXE], w[MAXE];
 #pragma unroll
           for (int e = 0; e < MAXE; ++e) {

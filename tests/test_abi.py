@@ -96,3 +96,23 @@ def test_stateless_entry_points_check_their_arguments_without_gpu():
     dims0 = (ctypes.c_int * 3)(4, 0, 2)
     assert lib.ctm_mlp_forward(one, 1, 2, dims0, W, None, one, one, None) == 1
     assert lib.ctm_mlp_forward(one, 0, 2, dims, W, None, one, one, None) == 1
+
+
+def test_mlp_work_size_and_training_argument_checks_without_gpu():
+    # host-only entry points of the warm-start training: the work size follows its layout (the
+    # hidden layers' pre-activations and activations, the output, two gradient buffers and 1024
+    # partial sums), and bad arguments are refused before any device work
+    from paper_2512_14414_gb300 import _lib
+    lib = _lib.load()
+    dims = (ctypes.c_int * 5)(32, 1024, 1024, 1024, 200)
+    batch = 8
+    expect = 2 * batch * 1024 * 3 + batch * 200 + 2 * batch * 1024 + 1024
+    assert lib.ctm_mlp_work_floats(batch, 4, dims) == expect
+    assert lib.ctm_mlp_work_floats(0, 4, dims) == -1
+    bad = (ctypes.c_int * 3)(4, 0, 2)
+    assert lib.ctm_mlp_work_floats(1, 2, bad) == -1
+    vp = ctypes.c_void_p
+    assert lib.ctm_mlp_backward(None, None, batch, 4, dims, None, None, None, None, None, None, None) == 1
+    assert lib.ctm_adam_step(None, None, None, None, 10, 1e-3, 0.9, 0.999, 1e-8, 1, None) == 1
+    assert lib.ctm_adam_step(vp(8), vp(8), vp(8), vp(8), 10, 1e-3, 0.9, 0.999, 1e-8, 0, None) == 1  # t < 1
+    assert lib.ctm_adam_step(vp(8), vp(8), vp(8), vp(8), 10, 1e-3, 1.0, 0.999, 1e-8, 1, None) == 1  # beta1 = 1

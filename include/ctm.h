@@ -11,10 +11,12 @@
  * evaluated on the nested single-layer network in which ket A and bra A* are
  * separate sites, joined by the crossing tensors X and Y (Eq. XY), contracted
  * by multisite CTMRG (Fig. 3) with projectors from QR + SVD (Eqs. PQ, QRSVD);
- * the gradient dE/dX is reverse mode through every CTMRG iteration (Eq. AD).
+ * the gradient dE/dX is reverse mode through every CTMRG iteration (Eq. AD),
+ * or, at a converged environment, the fixed-point gradient that the
+ * Discussion section proposes (ctm_grad_fixed_point).
  *
  * Layouts (all row-major, C order):
- *   site tensors   A: batch x (Lx*Ly) x [d][D][D][D][D]  = A[s][l][u][r][d];
+ *   site tensors   A: (Lx*Ly) x [d][D][D][D][D]  = A[s][l][u][r][d];
  *                  PEPS site (x, y) at index y*Lx + x.
  *   environment    per nested site (row-major over the 2Ly x 2Lx nested cell),
  *                  8 tensors in the order C_ul, T_u, C_ur, T_r, C_dr, T_d,

@@ -423,7 +423,7 @@ def main():
     roof = _roofline(prof, args.precision, peaks, kind, fp64_peak=fp64_peak)
     if roof is not None:
         roof["measured_on"] = f"one profiled step outside the timed region ({profiled_ms:.0f} ms with events)"
-    # the benchmark spec's two other fractions: tensor-core contractions and permutations
+    # the other kernel classes' fractions: tensor-core contractions, permutations, FP64 GEMM, Jacobi
     roof_other = {k: _roofline(prof, args.precision, peaks, kind, fp64_peak=fp64_peak, name=k)
                   for k in ("tc_gemm", "permute", "gemm_f64", "svd") if prof.get(k, (0, 0))[1]}
     cpu = None
